@@ -1,0 +1,336 @@
+"""Benchmark of the GDI annealing path (one JSON line on rank 0).
+
+A step is one gdi_anneal of the workload: initial state, all sweeps (thresholds, window selection,
+flips), exact-balance repair and cut, with the graph already resident on the device.  The metric
+is spin-updates per second (one update = one spin of one replica visited in one sweep).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl ours|reference]
+
+Multi-GPU runs (torchrun, one process per GPU) are replicas only: every rank anneals its own
+replica set of the same graph with its own seed, no data-path collective (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+# ---------------------------------------------------------------------------------------------
+# Workloads (synthetic stand-ins for the paper's G-set graphs; see the design doc for the recipes)
+WORKLOADS = {
+    # 2-D torus 100 x 100, +-1 weights, checkerboard colouring, 64 replicas, 5000 sweeps
+    "torus100_r64": dict(kind="torus", L=100, gseed=2002, A=1, B=4, W=1024, replicas=64,
+                         sweeps=5000, t0=12.0, t1=0.2, seed=1),
+    # Erdos-Renyi n = 800, p = 0.06, unit weights, greedy colouring, 1000 sweeps, 1 replica
+    "er800": dict(kind="er", n=800, p=0.06, gseed=1001, A=1, B=4, W=64, replicas=1, sweeps=1000,
+                  t0=12.0, t1=0.2, seed=1),
+}
+DEFAULT_WORKLOAD = "torus100_r64"
+
+
+def make_graph(wl):
+    from gdi_synth import erdos_renyi, torus2d
+    if wl["kind"] == "torus":
+        return torus2d(wl["L"], wl["gseed"], signed=True)
+    if wl["kind"] == "er":
+        return erdos_renyi(wl["n"], wl["p"], wl["gseed"])
+    raise ValueError(wl["kind"])
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+# ---------------------------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+
+        def rd():
+            for line in self.proc.stdout:
+                self.rows.append([x.strip() for x in line.split(",")])
+        self.thread = threading.Thread(target=rd, daemon=True)
+        self.thread.start()
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                for k, nm in enumerate(names):
+                    if r[5 + k].lower().startswith("active"):
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------------------------
+def oracle_throughput(g, wl, seconds: float = 12.0, processes: int | None = None):
+    """The oracle as it stands, timed on the host cores on a bounded sample of the workload: each
+    worker process anneals 4 replicas of the graph for as many sweeps of the same schedule as fit
+    the time budget (decided from a one-sweep probe).  Returns (updates/s, cores, sample text)."""
+    import multiprocessing as mp
+    import oracle
+    oracle.build()
+    cores = processes or os.cpu_count() or 1
+    R = min(4, wl["replicas"])
+    t = time.perf_counter()
+    oracle.anneal(g, A=wl["A"], B=wl["B"], W=wl["W"], t0=wl["t0"], t1=wl["t1"], sweeps=wl["sweeps"],
+                  seed=wl["seed"], replicas=R, color=g.color, last_sweep=1, trace=False, repair=False)
+    per_sweep = max(time.perf_counter() - t, 1e-4)
+    sweeps = int(max(1, min(wl["sweeps"], seconds / per_sweep)))
+    ctx = mp.get_context("spawn")
+    args = [(g, wl, R, sweeps, k) for k in range(cores)]
+    t0 = time.perf_counter()
+    with ctx.Pool(cores) as pool:
+        pool.map(_oracle_worker, args)
+    dt = time.perf_counter() - t0
+    updates = cores * R * sweeps * g.n
+    sample = (f"{cores} processes x {R} replicas x first {sweeps} of {wl['sweeps']} sweeps "
+              f"x {g.n} spins = {updates:.3e} updates in {dt:.1f} s")
+    return updates / dt, cores, sample
+
+
+def _oracle_worker(a):
+    g, wl, R, sweeps, k = a
+    import oracle
+    oracle.anneal(g, A=wl["A"], B=wl["B"], W=wl["W"], t0=wl["t0"], t1=wl["t1"], sweeps=wl["sweeps"],
+                  seed=wl["seed"] + 1000 * k, replicas=R, color=g.color, last_sweep=sweeps,
+                  trace=False, repair=False)
+    return 0
+
+
+# ---------------------------------------------------------------------------------------------
+def dist_setup(n_gpus):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend=backend)
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allreduce_max(x, world):
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def run_reference(args, wl, rank, world):
+    if rank != 0:
+        return
+    g = make_graph(wl)
+    for _ in range(args.warmup):
+        oracle_throughput(g, wl, seconds=2.0)
+    vals, samples = [], []
+    cores = 1
+    for _ in range(args.steps):
+        v, cores, s = oracle_throughput(g, wl, seconds=8.0)
+        vals.append(v)
+        samples.append(s)
+    value = statistics.mean(vals)
+    updates_per_step = wl["replicas"] * wl["sweeps"] * g.n
+    line = {"impl": "reference", "metric": "spin-updates/s", "value": value, "unit": "spin-updates/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * updates_per_step / value, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": config_of(args.workload, wl, g),
+            "cpu_baseline": {"value": value, "unit": "spin-updates/s", "cores": cores,
+                             "kind": "oracle", "sample": samples[-1]},
+            "e2e": {"value": value, "unit": "spin-updates/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def config_of(name, wl, g):
+    return {"workload": name, "n": g.n, "nnz": g.nnz, "replicas": wl["replicas"],
+            "sweeps": wl["sweeps"], "A": wl["A"], "B": wl["B"], "W": wl["W"],
+            "schedule": f"metropolis T {wl['t0']}->{wl['t1']} (3.0->0.05 in units of B)",
+            "l2": "L2 flushed (256 MiB write) before every timed step",
+            "parallelism": "replicas"}
+
+
+def run_ours(args, wl, rank, world, local):
+    import torch
+    import paper_1908_00210_gb300 as P
+    torch.cuda.set_device(local)
+    P.load()
+    g = make_graph(wl)
+    dev_props = torch.cuda.get_device_properties(local)
+    stream = torch.cuda.Stream()
+    seed = wl["seed"] + 7919 * rank
+    sch = P.Schedule(sweeps=wl["sweeps"], t0=wl["t0"], t1=wl["t1"])
+    ann = P.Annealer(g, A=wl["A"], B=wl["B"], W=wl["W"], replicas=wl["replicas"])
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")
+    updates = wl["replicas"] * wl["sweeps"] * g.n
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            ann.anneal(sch, seed, stream=stream)
+            ann.results()
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    wall0 = time.perf_counter()
+    ms = []
+    launches = 0
+    with torch.cuda.stream(stream):
+        for _ in range(args.steps):
+            flush.fill_(1)                              # evict the working set from L2
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ann.anneal(sch, seed, stream=stream)        # init kernel + anneal kernel
+            e1.record(stream)
+            launches += 2
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    clk = clocks.stop()
+    res = ann.results()
+    total_ms = sum(ms)
+    total_ms = allreduce_max(total_ms, world)
+    ms_per_step = total_ms / args.steps
+    value = world * updates / (ms_per_step / 1e3)
+
+    # end to end through the public API with host buffers: create from the host CSR (upload),
+    # anneal, read spins and results back (host pinned staging for the spins)
+    e2e_ms = []
+    h2d = g.row_ptr.nbytes + g.col.nbytes + g.w.nbytes + (g.color.nbytes if g.color is not None else 0)
+    d2h = wl["replicas"] * g.n + 24 * wl["replicas"]
+    for _ in range(max(1, min(args.steps, 3))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        a2 = P.Annealer(g, A=wl["A"], B=wl["B"], W=wl["W"], replicas=wl["replicas"])
+        a2.anneal(sch, seed, stream=stream)
+        a2.spins()
+        a2.results()
+        e2e_ms.append(1e3 * (time.perf_counter() - t0))
+        a2.close()
+    e2e_value = world * updates / (statistics.median(e2e_ms) / 1e3)
+
+    if rank != 0:
+        return
+    pk = peaks()
+    # roofline: the anneal is bound by integer issue (Philox, field gather from shared memory,
+    # threshold search and the window selection); see the design doc for the op count and the peak
+    ops_per_update = ALU_OPS_PER_UPDATE.get(args.workload, 100)
+    sm_max = float(pk.get("sm_max_mhz", 2070.0))
+    alu_peak = dev_props.multi_processor_count * 128 * sm_max * 1e6 / 1e12   # Tops/s
+    achieved = ops_per_update * (updates / (ms_per_step / 1e3)) / 1e12
+    try:
+        cpu_v, cores, sample = oracle_throughput(g, wl, seconds=12.0)
+        cpu = {"value": cpu_v, "unit": "spin-updates/s", "cores": cores, "kind": "oracle", "sample": sample}
+    except Exception as ex:  # the baseline is reported, not required
+        cpu = {"value": None, "unit": "spin-updates/s", "cores": 0, "kind": "oracle",
+               "sample": f"failed: {ex!r}"[:200]}
+    line = {
+        "metric": "spin-updates/s", "value": value, "unit": "spin-updates/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic", "config": config_of(args.workload, wl, g),
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s",
+                     "frac": achieved / alu_peak, "traffic": None,
+                     "ops_per_update": ops_per_update,
+                     "peak_note": "152 SMs x 128 int32 lanes x max SM clock (derived, see DESIGN.md)"},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": "spin-updates/s", "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h)},
+        "clocks": clk, "gpu_launches": launches,
+        "wall_s_timed_region": wall,
+        "result": {"final_cut_median": float(np.median(res["final_cut"])),
+                   "final_G_max_abs": int(np.abs(res["final_G"]).max()),
+                   "raw_G_max_abs": int(np.abs(res["raw_G"]).max())},
+    }
+    print(json.dumps(line), flush=True)
+    ann.close()
+
+
+# integer operations per spin update counted from the kernel source ("Roofline")
+ALU_OPS_PER_UPDATE = {"torus100_r64": 100, "er800": 300}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    args = ap.parse_args()
+    wl = WORKLOADS[args.workload]
+    rank, world, local = dist_setup(args.gpus)
+    if args.impl == "reference":
+        run_reference(args, wl, rank, world)
+    else:
+        run_ours(args, wl, rank, world, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,155 @@
+/*
+ * gdi.h -- C ABI of libgdi.so, a GB300 (sm_103a) implementation of the Globally Decoupled Ising
+ * (GDI) annealer for balanced min-cut graph bisection (Cook, Jin, Tan, arXiv:1908.00210).
+ *
+ * Problem (Section 3.1): split the vertices of G(V, E) into V1 (spin +1) and V2 (spin -1) with
+ * |V1| = |V2| and the smallest total weight of crossing edges.  The annealer minimises
+ *     H = A (sum_i s_i)^2 + B sum_<ij> w_ij (1 - s_i s_j) / 2              (Eq. 4, 5, 6)
+ * with Algorithm 3: the balance term reads one global magnetisation G = sum_i s_i that is updated
+ * by every flip, instead of the complete graph that Eq. 5 implies.
+ *
+ * Conventions shared by every entry point:
+ *   - Return value: 0 on success, a negative GDI_ERR_* code on failure.  No call aborts the
+ *     process; gdi_last_error() gives a one-line message for the calling thread's last failure.
+ *   - Ownership: gdi_create copies every input into buffers owned by the context; the caller may
+ *     free its own buffers when the call returns.  Outputs are written into caller buffers.
+ *   - Memory kind: arguments named *_mem say whether a pointer is host (GDI_MEM_HOST) or device
+ *     (GDI_MEM_DEVICE, a CUDA device pointer on the context's device).
+ *   - Streams: gdi_anneal enqueues all device work on the given CUDA stream and returns without
+ *     waiting; the getters synchronise that stream before reading.
+ *   - Vertex numbering: graphs are given in original vertex ids; spins come back in that order.
+ *   - Threads: a context may be used by one host thread at a time.
+ */
+#ifndef GDI_H
+#define GDI_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* error codes */
+#define GDI_OK 0
+#define GDI_ERR_INVALID_ARG   -1   /* null pointer, bad size, bad schedule, weight not +-1      */
+#define GDI_ERR_NOT_SYMMETRIC -2   /* (i,j,w) present without (j,i,w)                           */
+#define GDI_ERR_SELF_LOOP     -3
+#define GDI_ERR_DUP_EDGE      -4
+#define GDI_ERR_BAD_COLORING  -5   /* negative colour or two adjacent vertices share a colour    */
+#define GDI_ERR_OVERFLOW      -6   /* a size or an energy term would not fit the integer ranges  */
+#define GDI_ERR_OOM           -7
+#define GDI_ERR_CUDA          -8   /* a CUDA runtime call failed (message in gdi_last_error)     */
+#define GDI_ERR_TIMEOUT       -9   /* a bounded device wait gave up; the context stays usable    */
+#define GDI_ERR_NOT_ANNEALED  -10  /* a getter was called before any gdi_anneal                  */
+#define GDI_ERR_TOO_LARGE     -11  /* no kernel variant supports this size in this build          */
+
+/* memory kinds */
+#define GDI_MEM_HOST   0
+#define GDI_MEM_DEVICE 1
+
+/* schedule modes */
+#define GDI_METROPOLIS 0   /* accept with min(1, exp(-dE/T_s)), T_s geometric from t0 to t1          */
+#define GDI_PAPER_PF   1   /* Alg. 2/3: argmin, then flip with probability P_f; P_f geometric pf0->pf1 */
+
+/* gdi_run.flags */
+#define GDI_FLAG_TRACE     1  /* record per-sweep G, cut and state digest (slower; for parity)     */
+#define GDI_FLAG_NO_REPAIR 2  /* skip the exact-balance repair after the last sweep                */
+#define GDI_FLAG_CONTINUE  4  /* start from the spins the previous gdi_anneal left (resume)        */
+
+typedef struct gdi_ctx gdi_ctx;  /* opaque; owned by the library */
+
+/* A graph, or a batch of independent graphs given as one disjoint union.  Host pointers. */
+typedef struct {
+    int32_t num_instances;     /* >= 1                                                          */
+    const int64_t *inst_ptr;   /* [num_instances + 1] vertex offsets of the instances; may be
+                                  NULL when num_instances == 1                                  */
+    int64_t num_vertices;      /* N, total over instances                                       */
+    const int64_t *row_ptr;    /* [N + 1] CSR offsets                                           */
+    const int32_t *col;        /* [row_ptr[N]] neighbour ids (0..N-1, inside the same instance) */
+    const int32_t *weight;     /* [row_ptr[N]] edge weights, each +1 or -1; NULL = all +1       */
+    const int32_t *color;      /* [N] proper colouring (values >= 0, per instance); NULL = greedy
+                                  first-fit colouring in vertex-id order                        */
+} gdi_graph;
+
+/* Model constants of Eq. 4-6 and the decoupling window. */
+typedef struct {
+    int32_t A;          /* balance-penalty weight, >= 0 (Eq. 5)                                   */
+    int32_t B;          /* cut weight, >= 1 (Eq. 6)                                              */
+    int32_t W;          /* window: a colour class is updated in chunks of W consecutive ranks, each
+                           chunk seeing the exact running G in threshold order; 0 = whole class  */
+    int32_t replicas;   /* independent replicas per instance, >= 1                              */
+} gdi_model;
+
+/* Annealing schedule (Section 4.2; "reduce P_f" of Alg. 2/3 is the per-sweep table row). */
+typedef struct {
+    int32_t mode;       /* GDI_METROPOLIS or GDI_PAPER_PF                                         */
+    double t0, t1;      /* Metropolis temperatures at the first and last sweep, > 0              */
+    double pf0, pf1;    /* paper mode flip probabilities at the first and last sweep, in [0, 0.5) */
+    int32_t sweeps;     /* M >= 1                                                                 */
+} gdi_schedule;
+
+/* One annealing call. */
+typedef struct {
+    uint64_t seed;          /* Philox key; replica r of instance q draws counters (rank/4, sweep, q, r) */
+    int32_t first_sweep;    /* anneal sweeps [first_sweep, last_sweep) of the schedule            */
+    int32_t last_sweep;     /* <= 0 means schedule.sweeps                                         */
+    int32_t flags;          /* GDI_FLAG_*                                                         */
+    const int8_t *init_spins; /* [replicas][N] spins (+1/-1) in original order, or NULL: balanced
+                                 random start (ignored with GDI_FLAG_CONTINUE)                    */
+    int32_t init_mem;       /* GDI_MEM_HOST or GDI_MEM_DEVICE for init_spins                       */
+    void *stream;           /* cudaStream_t for all device work; NULL = the legacy default stream */
+} gdi_run;
+
+/* Build a context: validate the CSR (symmetric, no self-loops, no duplicates, weights +-1),
+ * colour it (or check the given colouring), relabel every instance into rank order (colour asc,
+ * vertex id asc), and copy it to the current CUDA device.  Host-side preprocessing; blocking. */
+int gdi_create(gdi_ctx **out, const gdi_graph *graph, const gdi_model *model);
+
+/* Anneal every replica of every instance with Algorithm 3, serialised deterministically: colour
+ * classes in order, windows of W ranks, and inside a window the exact running G seen in threshold
+ * order (+1 group first on even sweeps); then repair to exact balance |G| = n mod 2 and compute
+ * the cut.
+ * Enqueued on run->stream; returns without waiting.  Host pointers in `run` are read before the
+ * call returns. */
+int gdi_anneal(gdi_ctx *ctx, const gdi_schedule *schedule, const gdi_run *run);
+
+/* Spins after the last gdi_anneal, [replicas][N] in original vertex order (+1 = V1, -1 = V2,
+ * Section 3.1).  Synchronises the run stream. */
+int gdi_get_spins(gdi_ctx *ctx, int8_t *out, int32_t out_mem);
+
+/* Per (instance, replica), index q * replicas + r: raw G after the last sweep, G after repair,
+ * cut before and after repair (cut = sum of crossing edge weights, Section 5).  Any pointer may be
+ * NULL.  Host pointers.  Synchronises the run stream. */
+int gdi_get_results(gdi_ctx *ctx, int32_t *raw_G, int32_t *final_G, int64_t *raw_cut,
+                    int64_t *final_cut);
+
+/* Cut after repair of one (instance, replica). */
+int gdi_cut(gdi_ctx *ctx, int32_t instance, int32_t replica, int64_t *cut_out);
+
+/* Magnetisation G = |V1| - |V2| before (raw) and after the repair of one (instance, replica). */
+int gdi_balance(gdi_ctx *ctx, int32_t instance, int32_t replica, int32_t *raw_G, int32_t *final_G);
+
+/* Per-sweep trace of the last gdi_anneal with GDI_FLAG_TRACE: [q * replicas + r][sweeps] arrays of
+ * the state digest, G and cut after each sweep (entries outside the annealed range are 0).
+ * digest = sum over ranks i with s_i = +1 of splitmix64(i | sweep << 32 | replica << 48) mod 2^64.
+ * Any pointer may be NULL.  Host pointers. */
+int gdi_get_trace(gdi_ctx *ctx, uint64_t *digest, int32_t *G, int64_t *cut);
+
+/* Context facts: number of colour classes per instance (host [num_instances], may be NULL),
+ * the largest degree, and the E_cap of the last schedule (0 before any anneal). */
+int gdi_info(gdi_ctx *ctx, int32_t *num_classes, int32_t *max_degree, int32_t *ecap);
+
+/* Free the context and its device buffers (synchronises the run stream first). */
+void gdi_destroy(gdi_ctx *ctx);
+
+/* Static description of an error code. */
+const char *gdi_strerror(int code);
+
+/* Message of the calling thread's last failed call ("" if none). */
+const char *gdi_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GDI_H */

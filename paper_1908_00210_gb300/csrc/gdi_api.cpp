@@ -1,0 +1,619 @@
+// gdi_api.cpp -- host side of libgdi.so: the C ABI declared in include/gdi.h.
+//
+// gdi_create validates the CSR, colours it (greedy first-fit in vertex-id order unless a colouring
+// is given), relabels every instance into rank order (colour asc, id asc), packs each neighbour as
+// (local rank | weight-sign bit) and uploads the rank-space CSR once.  gdi_anneal builds the
+// per-sweep threshold table on the host (double precision; the GPU never evaluates exp), then
+// enqueues the initial-state kernel and the persistent anneal kernel on the caller's stream.
+#include "gdi.h"
+#include "gdi_internal.h"
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string &msg)
+{
+    g_last_error = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what)
+{
+    return fail(GDI_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+template <typename T>
+struct DevBuf {
+    T *p = nullptr;
+    size_t n = 0;
+    cudaError_t alloc(size_t count)
+    {
+        if (count <= n && p) return cudaSuccess;
+        release();
+        const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+        cudaError_t e = cudaMalloc((void **)&p, bytes);
+        if (e == cudaSuccess) n = count; else p = nullptr;
+        return e;
+    }
+    void release()
+    {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+};
+
+}  // namespace
+
+struct gdi_ctx {
+    int device = 0;
+    int32_t Q = 0, R = 1, A = 0, B = 1, W = 0;
+    int64_t N = 0, nnz = 0;
+    int32_t max_n = 0, max_window = 0, max_degree = 0;
+    std::vector<int32_t> num_classes;       // per instance
+    DevBuf<int64_t> node_off, row_ptr;
+    DevBuf<int32_t> class_off, class_ptr, rank_of;
+    DevBuf<uint32_t> col;
+    DevBuf<int8_t> spins, init_stage, out_stage;
+    DevBuf<uint32_t> tab;
+    DevBuf<int32_t> tab_off;
+    DevBuf<int32_t> raw_G, final_G, tr_G, err;
+    DevBuf<int64_t> raw_cut, final_cut, tr_cut;
+    DevBuf<uint64_t> tr_digest;
+    int32_t last_sweeps = 0, last_flags = 0, ecap = 0;
+    bool annealed = false;
+    cudaStream_t stream = nullptr;
+    int block = 256;
+    int grid_limit = 0;
+    int last_grid = 0;
+    size_t last_smem = 0;
+
+    GdiDevProblem problem() const
+    {
+        GdiDevProblem P;
+        P.num_instances = Q;
+        P.replicas = R;
+        P.N = N;
+        P.node_off = node_off.p;
+        P.class_off = class_off.p;
+        P.class_ptr = class_ptr.p;
+        P.row_ptr = row_ptr.p;
+        P.col = col.p;
+        P.rank_of = rank_of.p;
+        P.A = A;
+        P.B = B;
+        P.W = W;
+        P.max_n = max_n;
+        P.max_window = max_window;
+        P.max_degree = max_degree;
+        return P;
+    }
+    void release()
+    {
+        node_off.release(); row_ptr.release(); class_off.release(); class_ptr.release();
+        rank_of.release(); col.release(); spins.release(); init_stage.release(); out_stage.release();
+        tab.release(); tab_off.release(); raw_G.release(); final_G.release(); tr_G.release();
+        err.release(); raw_cut.release(); final_cut.release(); tr_cut.release(); tr_digest.release();
+    }
+};
+
+namespace {
+
+// ---------------------------------------------------------------------------------------------
+// Threshold table.  Metropolis row s holds thr_s(dE) = floor(exp(-dE / T_s) 2^32) for dE = 1, 2, ...
+// while it is non-zero (thr = 2^32 for dE <= 0 is implicit); T_s = t0 (t1/t0)^(s/(M-1)).
+// Paper row s holds thr for dE = -1, 0, +1: 2^32 - p, 2^31, p with p = floor(P_f,s 2^32) + 1
+// (argmin, then the random flip "u <= P_f" of Section 4.2), P_f,s = pf0 (pf1/pf0)^(s/(M-1)).
+double sched_at(double v0, double v1, int s, int M)
+{
+    if (M <= 1 || v0 == v1) return v0;
+    return v0 * std::pow(v1 / v0, (double)s / (double)(M - 1));
+}
+
+int build_table(const gdi_schedule &S, std::vector<uint32_t> &tab, std::vector<int32_t> &off,
+                int32_t &ecap, int32_t &max_row)
+{
+    const int M = S.sweeps;
+    tab.clear();
+    off.assign((size_t)M + 1, 0);
+    max_row = 0;
+    if (S.mode == GDI_METROPOLIS) {
+        if (!(S.t0 > 0.0) || !(S.t1 > 0.0) || !std::isfinite(S.t0) || !std::isfinite(S.t1))
+            return fail(GDI_ERR_INVALID_ARG, "Metropolis temperatures must be finite and > 0");
+        for (int s = 0; s < M; ++s) {
+            off[s] = (int32_t)tab.size();
+            const double T = sched_at(S.t0, S.t1, s, M);
+            for (int64_t E = 1;; ++E) {
+                const double t = std::floor(std::exp(-(double)E / T) * 4294967296.0);
+                if (t <= 0.0) break;
+                if (E > (1 << 22)) return fail(GDI_ERR_OVERFLOW, "temperature too high for the table");
+                tab.push_back((uint32_t)t);
+            }
+            max_row = std::max<int32_t>(max_row, (int32_t)tab.size() - off[s]);
+            if (tab.size() > (size_t)1 << 28) return fail(GDI_ERR_OVERFLOW, "threshold table too large");
+        }
+        off[M] = (int32_t)tab.size();
+        ecap = max_row + 1;
+        return GDI_OK;
+    }
+    if (S.mode == GDI_PAPER_PF) {
+        if (!(S.pf0 >= 0 && S.pf0 < 0.5 && S.pf1 >= 0 && S.pf1 < 0.5))
+            return fail(GDI_ERR_INVALID_ARG, "P_f must lie in [0, 0.5)");
+        if (S.pf0 != S.pf1 && (S.pf0 <= 0 || S.pf1 <= 0))
+            return fail(GDI_ERR_INVALID_ARG, "a geometric P_f schedule needs pf0, pf1 > 0");
+        for (int s = 0; s < M; ++s) {
+            off[s] = (int32_t)tab.size();
+            const double pf = sched_at(S.pf0, S.pf1, s, M);
+            uint64_t p = (uint64_t)std::floor(pf * 4294967296.0) + 1;
+            if (p > ((uint64_t)1 << 32)) p = (uint64_t)1 << 32;
+            tab.push_back((uint32_t)(((uint64_t)1 << 32) - p));
+            tab.push_back(0x80000000u);
+            tab.push_back((uint32_t)p);
+        }
+        off[M] = (int32_t)tab.size();
+        max_row = 3;
+        ecap = 1;
+        return GDI_OK;
+    }
+    return fail(GDI_ERR_INVALID_ARG, "unknown schedule mode");
+}
+
+// ---------------------------------------------------------------------------------------------
+// CSR validation: ids inside the instance, no self-loops, no duplicates, weights +-1, symmetric.
+int validate_graph(const gdi_graph &g, const std::vector<int64_t> &inst, std::vector<int32_t> &w)
+{
+    const int64_t N = g.num_vertices;
+    if (g.row_ptr[0] != 0) return fail(GDI_ERR_INVALID_ARG, "row_ptr[0] must be 0");
+    for (int64_t v = 0; v < N; ++v)
+        if (g.row_ptr[v + 1] < g.row_ptr[v]) return fail(GDI_ERR_INVALID_ARG, "row_ptr not monotone");
+    const int64_t nnz = g.row_ptr[N];
+    w.resize((size_t)nnz);
+    for (int64_t e = 0; e < nnz; ++e) {
+        const int32_t x = g.weight ? g.weight[e] : 1;
+        if (x != 1 && x != -1) return fail(GDI_ERR_INVALID_ARG, "edge weights must be +1 or -1");
+        w[(size_t)e] = x;
+    }
+    std::vector<int64_t> stamp((size_t)N, -1);
+    size_t q = 0;
+    for (int64_t v = 0; v < N; ++v) {
+        while (inst[q + 1] <= v) ++q;
+        for (int64_t e = g.row_ptr[v]; e < g.row_ptr[v + 1]; ++e) {
+            const int64_t j = g.col[e];
+            if (j < inst[q] || j >= inst[q + 1])
+                return fail(GDI_ERR_INVALID_ARG, "neighbour id outside its instance (vertex " + std::to_string(v) + ")");
+            if (j == v) return fail(GDI_ERR_SELF_LOOP, "self-loop at vertex " + std::to_string(v));
+            if (stamp[(size_t)j] == v)
+                return fail(GDI_ERR_DUP_EDGE, "duplicate edge " + std::to_string(v) + "-" + std::to_string(j));
+            stamp[(size_t)j] = v;
+        }
+    }
+    // symmetry: per row a sorted copy (by neighbour), then each (v, j, w) must find (j, v, w)
+    std::vector<int32_t> sc((size_t)nnz);
+    std::vector<int32_t> sw((size_t)nnz);
+    std::vector<int64_t> idx;
+    for (int64_t v = 0; v < N; ++v) {
+        const int64_t e0 = g.row_ptr[v], e1 = g.row_ptr[v + 1];
+        idx.resize((size_t)(e1 - e0));
+        for (int64_t e = e0; e < e1; ++e) idx[(size_t)(e - e0)] = e;
+        std::sort(idx.begin(), idx.end(), [&](int64_t a, int64_t b) { return g.col[a] < g.col[b]; });
+        for (int64_t k = 0; k < e1 - e0; ++k) {
+            sc[(size_t)(e0 + k)] = g.col[idx[(size_t)k]];
+            sw[(size_t)(e0 + k)] = w[(size_t)idx[(size_t)k]];
+        }
+    }
+    for (int64_t v = 0; v < N; ++v) {
+        for (int64_t e = g.row_ptr[v]; e < g.row_ptr[v + 1]; ++e) {
+            const int64_t j = sc[(size_t)e];
+            const int32_t *b = sc.data() + g.row_ptr[j];
+            const int32_t *en = sc.data() + g.row_ptr[j + 1];
+            const int32_t *f = std::lower_bound(b, en, (int32_t)v);
+            if (f == en || *f != v || sw[(size_t)(f - sc.data())] != sw[(size_t)e])
+                return fail(GDI_ERR_NOT_SYMMETRIC, "edge " + std::to_string(v) + "-" + std::to_string(j) +
+                                                       " has no mirror with the same weight");
+        }
+    }
+    return GDI_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int gdi_create(gdi_ctx **out, const gdi_graph *g, const gdi_model *m)
+{
+    if (!out || !g || !m) return fail(GDI_ERR_INVALID_ARG, "null argument");
+    *out = nullptr;
+    if (g->num_instances < 1 || g->num_vertices < 1 || !g->row_ptr || !g->col)
+        return fail(GDI_ERR_INVALID_ARG, "empty graph or missing CSR arrays");
+    if (g->num_instances > 1 && !g->inst_ptr) return fail(GDI_ERR_INVALID_ARG, "inst_ptr required for a batch");
+    if (m->A < 0 || m->B < 1 || m->W < 0 || m->replicas < 1)
+        return fail(GDI_ERR_INVALID_ARG, "need A >= 0, B >= 1, W >= 0, replicas >= 1");
+    if (m->A > (1 << 20) || m->B > (1 << 20)) return fail(GDI_ERR_OVERFLOW, "A or B too large");
+    const int32_t Q = g->num_instances;
+    const int64_t N = g->num_vertices;
+    std::vector<int64_t> inst((size_t)Q + 1);
+    if (g->inst_ptr) {
+        for (int32_t q = 0; q <= Q; ++q) inst[(size_t)q] = g->inst_ptr[q];
+    } else {
+        inst[0] = 0;
+        inst[1] = N;
+    }
+    if (inst[0] != 0 || inst[(size_t)Q] != N) return fail(GDI_ERR_INVALID_ARG, "inst_ptr must run from 0 to N");
+    for (int32_t q = 0; q < Q; ++q) {
+        if (inst[(size_t)q + 1] <= inst[(size_t)q]) return fail(GDI_ERR_INVALID_ARG, "empty instance");
+        if (inst[(size_t)q + 1] - inst[(size_t)q] > (1 << 28)) return fail(GDI_ERR_OVERFLOW, "instance over 2^28 vertices");
+    }
+    if ((int64_t)m->replicas * N > ((int64_t)1 << 40)) return fail(GDI_ERR_OVERFLOW, "replicas * N too large");
+
+    std::vector<int32_t> w;
+    int rc = validate_graph(*g, inst, w);
+    if (rc) return rc;
+
+    // colouring: caller's (checked) or greedy first-fit in id order, per instance
+    std::vector<int32_t> color((size_t)N);
+    if (g->color) {
+        for (int64_t v = 0; v < N; ++v) {
+            if (g->color[v] < 0) return fail(GDI_ERR_BAD_COLORING, "negative colour");
+            color[(size_t)v] = g->color[v];
+        }
+    } else {
+        std::vector<int64_t> mark;
+        for (int64_t v = 0; v < N; ++v) {
+            const int64_t d = g->row_ptr[v + 1] - g->row_ptr[v];
+            if ((int64_t)mark.size() < d + 2) mark.resize((size_t)d + 2, -1);
+            for (int64_t e = g->row_ptr[v]; e < g->row_ptr[v + 1]; ++e) {
+                const int64_t j = g->col[e];
+                if (j < v) {
+                    const int32_t c = color[(size_t)j];
+                    if (c < d + 2) mark[(size_t)c] = v;
+                }
+            }
+            int32_t c = 0;
+            while (mark[(size_t)c] == v) ++c;
+            color[(size_t)v] = c;
+        }
+    }
+    for (int64_t v = 0; v < N; ++v)
+        for (int64_t e = g->row_ptr[v]; e < g->row_ptr[v + 1]; ++e)
+            if (color[(size_t)g->col[e]] == color[(size_t)v])
+                return fail(GDI_ERR_BAD_COLORING, "adjacent vertices share a colour");
+
+    gdi_ctx *c = new (std::nothrow) gdi_ctx;
+    if (!c) return fail(GDI_ERR_OOM, "host allocation failed");
+    cudaGetDevice(&c->device);
+    c->Q = Q;
+    c->R = m->replicas;
+    c->A = m->A;
+    c->B = m->B;
+    c->W = m->W;
+    c->N = N;
+    c->nnz = g->row_ptr[N];
+
+    // rank order per instance: counting sort by colour, stable in id
+    std::vector<int32_t> rank_of((size_t)N), vert_of((size_t)N);
+    std::vector<int32_t> class_off((size_t)Q + 1, 0), class_ptr;
+    c->num_classes.assign((size_t)Q, 0);
+    for (int32_t q = 0; q < Q; ++q) {
+        const int64_t lo = inst[(size_t)q], hi = inst[(size_t)q + 1];
+        const int32_t n = (int32_t)(hi - lo);
+        int32_t ncol = 0;
+        for (int64_t v = lo; v < hi; ++v) ncol = std::max(ncol, color[(size_t)v] + 1);
+        if ((int64_t)ncol > (int64_t)n + 1 && ncol > (1 << 24)) {
+            delete c;
+            return fail(GDI_ERR_OVERFLOW, "colour values too large");
+        }
+        std::vector<int32_t> cnt((size_t)ncol + 1, 0);
+        for (int64_t v = lo; v < hi; ++v) cnt[(size_t)color[(size_t)v] + 1]++;
+        for (int32_t k = 0; k < ncol; ++k) cnt[(size_t)k + 1] += cnt[(size_t)k];
+        class_off[(size_t)q] = (int32_t)class_ptr.size();
+        int32_t nclass = 0;
+        for (int32_t k = 0; k < ncol; ++k) {
+            if (cnt[(size_t)k + 1] > cnt[(size_t)k]) {
+                class_ptr.push_back(cnt[(size_t)k]);
+                const int32_t sz = cnt[(size_t)k + 1] - cnt[(size_t)k];
+                c->max_window = std::max(c->max_window, m->W > 0 ? std::min(m->W, sz) : sz);
+                ++nclass;
+            }
+        }
+        class_ptr.push_back(n);
+        c->num_classes[(size_t)q] = nclass;
+        for (int64_t v = lo; v < hi; ++v) {
+            const int32_t r = cnt[(size_t)color[(size_t)v]]++;
+            rank_of[(size_t)v] = (int32_t)(lo + r);
+            vert_of[(size_t)(lo + r)] = (int32_t)v;
+        }
+        c->max_n = std::max(c->max_n, n);
+    }
+    class_off[(size_t)Q] = (int32_t)class_ptr.size();
+
+    // rank-space CSR, neighbour = local rank | weight-sign bit
+    std::vector<int64_t> rp((size_t)N + 1, 0);
+    std::vector<uint32_t> cr((size_t)c->nnz);
+    {
+        size_t q = 0;
+        int64_t e_out = 0;
+        for (int64_t r = 0; r < N; ++r) {
+            while (inst[q + 1] <= r) ++q;
+            const int64_t v = vert_of[(size_t)r];
+            rp[(size_t)r] = e_out;
+            const int64_t d = g->row_ptr[v + 1] - g->row_ptr[v];
+            c->max_degree = (int32_t)std::max<int64_t>(c->max_degree, d);
+            for (int64_t e = g->row_ptr[v]; e < g->row_ptr[v + 1]; ++e) {
+                const uint32_t lr = (uint32_t)(rank_of[(size_t)g->col[e]] - inst[q]);
+                cr[(size_t)e_out++] = lr | (w[(size_t)e] < 0 ? 0x80000000u : 0u);
+            }
+        }
+        rp[(size_t)N] = e_out;
+    }
+
+    cudaError_t e;
+#define GDI_UP(buf, vec)                                                                          \
+    do {                                                                                          \
+        e = buf.alloc(vec.size());                                                                \
+        if (e == cudaSuccess && !vec.empty())                                                     \
+            e = cudaMemcpy(buf.p, vec.data(), vec.size() * sizeof(vec[0]), cudaMemcpyHostToDevice); \
+        if (e != cudaSuccess) {                                                                   \
+            c->release();                                                                         \
+            delete c;                                                                             \
+            return e == cudaErrorMemoryAllocation ? fail(GDI_ERR_OOM, "device allocation failed")  \
+                                                  : cuda_fail(e, "upload");                       \
+        }                                                                                         \
+    } while (0)
+    GDI_UP(c->node_off, inst);
+    GDI_UP(c->row_ptr, rp);
+    GDI_UP(c->col, cr);
+    GDI_UP(c->class_off, class_off);
+    GDI_UP(c->class_ptr, class_ptr);
+    GDI_UP(c->rank_of, rank_of);
+#undef GDI_UP
+    e = c->spins.alloc((size_t)c->R * (size_t)N);
+    if (e == cudaSuccess) e = c->raw_G.alloc((size_t)Q * c->R);
+    if (e == cudaSuccess) e = c->final_G.alloc((size_t)Q * c->R);
+    if (e == cudaSuccess) e = c->raw_cut.alloc((size_t)Q * c->R);
+    if (e == cudaSuccess) e = c->final_cut.alloc((size_t)Q * c->R);
+    if (e == cudaSuccess) e = c->err.alloc(4);
+    if (e != cudaSuccess) {
+        c->release();
+        delete c;
+        return fail(GDI_ERR_OOM, "device allocation failed");
+    }
+    *out = c;
+    return GDI_OK;
+}
+
+int gdi_anneal(gdi_ctx *c, const gdi_schedule *S, const gdi_run *run)
+{
+    if (!c || !S || !run) return fail(GDI_ERR_INVALID_ARG, "null argument");
+    if (S->sweeps < 1) return fail(GDI_ERR_INVALID_ARG, "sweeps must be >= 1");
+    const int32_t s_begin = run->first_sweep;
+    const int32_t s_end = run->last_sweep > 0 ? run->last_sweep : S->sweeps;
+    if (s_begin < 0 || s_end > S->sweeps || s_begin > s_end)
+        return fail(GDI_ERR_INVALID_ARG, "sweep range outside the schedule");
+    const bool cont = (run->flags & GDI_FLAG_CONTINUE) != 0;
+    if (cont && !c->annealed) return fail(GDI_ERR_NOT_ANNEALED, "GDI_FLAG_CONTINUE before any anneal");
+    if (!cont && !run->init_spins && s_begin != 0)
+        return fail(GDI_ERR_INVALID_ARG, "a random start must begin at sweep 0");
+
+    std::vector<uint32_t> tab;
+    std::vector<int32_t> off;
+    int32_t ecap = 0, max_row = 0;
+    int rc = build_table(*S, tab, off, ecap, max_row);
+    if (rc) return rc;
+    // integer ranges: |B h + 4A - E*| and |G| must stay far below the 2^30 threshold sentinels
+    if ((int64_t)c->B * c->max_degree + 4LL * c->A + ecap >= ((int64_t)1 << 29))
+        return fail(GDI_ERR_OVERFLOW, "B * max_degree + 4A + E_cap must stay below 2^29");
+
+    cudaStream_t st = (cudaStream_t)run->stream;
+    cudaError_t e = c->tab.alloc(tab.size());
+    if (e == cudaSuccess) e = c->tab_off.alloc(off.size());
+    if (e != cudaSuccess) return fail(GDI_ERR_OOM, "device allocation failed (table)");
+    // pageable source: the copy is staged before cudaMemcpyAsync returns
+    e = cudaMemcpyAsync(c->tab.p, tab.data(), tab.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->tab_off.p, off.data(), off.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "table upload");
+
+    const bool trace = (run->flags & GDI_FLAG_TRACE) != 0;
+    const size_t items = (size_t)c->Q * c->R;
+    if (trace) {
+        e = c->tr_digest.alloc(items * S->sweeps);
+        if (e == cudaSuccess) e = c->tr_G.alloc(items * S->sweeps);
+        if (e == cudaSuccess) e = c->tr_cut.alloc(items * S->sweeps);
+        if (e != cudaSuccess) return fail(GDI_ERR_OOM, "device allocation failed (trace)");
+        cudaMemsetAsync(c->tr_digest.p, 0, items * S->sweeps * sizeof(uint64_t), st);
+        cudaMemsetAsync(c->tr_G.p, 0, items * S->sweeps * sizeof(int32_t), st);
+        cudaMemsetAsync(c->tr_cut.p, 0, items * S->sweeps * sizeof(int64_t), st);
+    }
+    const GdiDevProblem P = c->problem();
+    const uint32_t key0 = (uint32_t)run->seed, key1 = (uint32_t)(run->seed >> 32);
+    if (!cont) {
+        const int8_t *init = nullptr;
+        if (run->init_spins) {
+            const size_t bytes = (size_t)c->R * (size_t)c->N;
+            if (run->init_mem == GDI_MEM_DEVICE) {
+                init = run->init_spins;
+            } else {
+                e = c->init_stage.alloc(bytes);
+                if (e == cudaSuccess)
+                    e = cudaMemcpyAsync(c->init_stage.p, run->init_spins, bytes, cudaMemcpyHostToDevice, st);
+                if (e != cudaSuccess) return cuda_fail(e, "init spins upload");
+                init = c->init_stage.p;
+            }
+        }
+        int ke = gdi_launch_init(P, c->spins.p, init, init ? 1 : 0, key0, key1, st);
+        if (ke) return cuda_fail((cudaError_t)ke, "init kernel");
+    }
+
+    GdiDevRun R;
+    R.spins = c->spins.p;
+    R.tab = c->tab.p;
+    R.tab_off = c->tab_off.p;
+    R.mode = S->mode;
+    R.sweeps = S->sweeps;
+    R.s_begin = s_begin;
+    R.s_end = s_end;
+    R.max_row = max_row;
+    R.key0 = key0;
+    R.key1 = key1;
+    R.flags = (trace ? GDI_DEV_TRACE : 0) | ((run->flags & GDI_FLAG_NO_REPAIR) ? GDI_DEV_NO_REPAIR : 0);
+    R.raw_G = c->raw_G.p;
+    R.final_G = c->final_G.p;
+    R.raw_cut = c->raw_cut.p;
+    R.final_cut = c->final_cut.p;
+    R.tr_digest = trace ? c->tr_digest.p : nullptr;
+    R.tr_G = trace ? c->tr_G.p : nullptr;
+    R.tr_cut = trace ? c->tr_cut.p : nullptr;
+    R.err = c->err.p;
+
+    size_t need = 0;
+    int H = 0;
+    gdi_cta_smem_bytes(P, R, c->block, &need, &H);
+    int max_optin = 0;
+    cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
+    if (need > (size_t)max_optin)
+        return fail(GDI_ERR_TOO_LARGE, "instance needs " + std::to_string(need) +
+                                           " bytes of shared memory per block (limit " +
+                                           std::to_string(max_optin) + ")");
+    int ke = gdi_launch_cta_anneal(P, R, c->block, c->grid_limit, st, &c->last_grid, &c->last_smem);
+    if (ke) return cuda_fail((cudaError_t)ke, "anneal kernel launch");
+    c->stream = st;
+    c->annealed = true;
+    c->last_sweeps = S->sweeps;
+    c->last_flags = run->flags;
+    c->ecap = ecap;
+    return GDI_OK;
+}
+
+static int sync_ctx(gdi_ctx *c)
+{
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
+    return GDI_OK;
+}
+
+int gdi_get_spins(gdi_ctx *c, int8_t *out, int32_t out_mem)
+{
+    if (!c || !out) return fail(GDI_ERR_INVALID_ARG, "null argument");
+    if (!c->annealed) return fail(GDI_ERR_NOT_ANNEALED, "no anneal yet");
+    const size_t bytes = (size_t)c->R * (size_t)c->N;
+    int8_t *dst = out;
+    if (out_mem != GDI_MEM_DEVICE) {
+        cudaError_t e = c->out_stage.alloc(bytes);
+        if (e != cudaSuccess) return fail(GDI_ERR_OOM, "device allocation failed");
+        dst = c->out_stage.p;
+    }
+    int ke = gdi_launch_gather_spins(c->problem(), c->spins.p, dst, c->stream);
+    if (ke) return cuda_fail((cudaError_t)ke, "gather kernel");
+    if (out_mem != GDI_MEM_DEVICE) {
+        cudaError_t e = cudaMemcpyAsync(out, dst, bytes, cudaMemcpyDeviceToHost, c->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "spins download");
+    }
+    return sync_ctx(c);
+}
+
+int gdi_get_results(gdi_ctx *c, int32_t *raw_G, int32_t *final_G, int64_t *raw_cut, int64_t *final_cut)
+{
+    if (!c) return fail(GDI_ERR_INVALID_ARG, "null argument");
+    if (!c->annealed) return fail(GDI_ERR_NOT_ANNEALED, "no anneal yet");
+    int rc = sync_ctx(c);
+    if (rc) return rc;
+    const size_t items = (size_t)c->Q * c->R;
+    cudaError_t e = cudaSuccess;
+    if (raw_G && e == cudaSuccess) e = cudaMemcpy(raw_G, c->raw_G.p, items * 4, cudaMemcpyDeviceToHost);
+    if (final_G && e == cudaSuccess) e = cudaMemcpy(final_G, c->final_G.p, items * 4, cudaMemcpyDeviceToHost);
+    if (raw_cut && e == cudaSuccess) e = cudaMemcpy(raw_cut, c->raw_cut.p, items * 8, cudaMemcpyDeviceToHost);
+    if (final_cut && e == cudaSuccess) e = cudaMemcpy(final_cut, c->final_cut.p, items * 8, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "results download");
+    return GDI_OK;
+}
+
+int gdi_cut(gdi_ctx *c, int32_t instance, int32_t replica, int64_t *cut_out)
+{
+    if (!c || !cut_out || instance < 0 || instance >= c->Q || replica < 0 || replica >= c->R)
+        return fail(GDI_ERR_INVALID_ARG, "bad instance/replica");
+    if (!c->annealed) return fail(GDI_ERR_NOT_ANNEALED, "no anneal yet");
+    int rc = sync_ctx(c);
+    if (rc) return rc;
+    cudaError_t e = cudaMemcpy(cut_out, c->final_cut.p + (size_t)instance * c->R + replica, 8,
+                               cudaMemcpyDeviceToHost);
+    return e == cudaSuccess ? GDI_OK : cuda_fail(e, "cut download");
+}
+
+int gdi_balance(gdi_ctx *c, int32_t instance, int32_t replica, int32_t *raw_G, int32_t *final_G)
+{
+    if (!c || instance < 0 || instance >= c->Q || replica < 0 || replica >= c->R)
+        return fail(GDI_ERR_INVALID_ARG, "bad instance/replica");
+    if (!c->annealed) return fail(GDI_ERR_NOT_ANNEALED, "no anneal yet");
+    int rc = sync_ctx(c);
+    if (rc) return rc;
+    const size_t i = (size_t)instance * c->R + replica;
+    cudaError_t e = cudaSuccess;
+    if (raw_G) e = cudaMemcpy(raw_G, c->raw_G.p + i, 4, cudaMemcpyDeviceToHost);
+    if (final_G && e == cudaSuccess) e = cudaMemcpy(final_G, c->final_G.p + i, 4, cudaMemcpyDeviceToHost);
+    return e == cudaSuccess ? GDI_OK : cuda_fail(e, "balance download");
+}
+
+int gdi_get_trace(gdi_ctx *c, uint64_t *digest, int32_t *G, int64_t *cut)
+{
+    if (!c) return fail(GDI_ERR_INVALID_ARG, "null argument");
+    if (!c->annealed) return fail(GDI_ERR_NOT_ANNEALED, "no anneal yet");
+    if (!(c->last_flags & GDI_FLAG_TRACE)) return fail(GDI_ERR_INVALID_ARG, "last anneal had no GDI_FLAG_TRACE");
+    int rc = sync_ctx(c);
+    if (rc) return rc;
+    const size_t cnt = (size_t)c->Q * c->R * c->last_sweeps;
+    cudaError_t e = cudaSuccess;
+    if (digest) e = cudaMemcpy(digest, c->tr_digest.p, cnt * 8, cudaMemcpyDeviceToHost);
+    if (G && e == cudaSuccess) e = cudaMemcpy(G, c->tr_G.p, cnt * 4, cudaMemcpyDeviceToHost);
+    if (cut && e == cudaSuccess) e = cudaMemcpy(cut, c->tr_cut.p, cnt * 8, cudaMemcpyDeviceToHost);
+    return e == cudaSuccess ? GDI_OK : cuda_fail(e, "trace download");
+}
+
+int gdi_info(gdi_ctx *c, int32_t *num_classes, int32_t *max_degree, int32_t *ecap)
+{
+    if (!c) return fail(GDI_ERR_INVALID_ARG, "null argument");
+    if (num_classes) std::memcpy(num_classes, c->num_classes.data(), c->num_classes.size() * 4);
+    if (max_degree) *max_degree = c->max_degree;
+    if (ecap) *ecap = c->ecap;
+    return GDI_OK;
+}
+
+void gdi_destroy(gdi_ctx *c)
+{
+    if (!c) return;
+    if (c->annealed) cudaStreamSynchronize(c->stream);
+    c->release();
+    delete c;
+}
+
+const char *gdi_strerror(int code)
+{
+    switch (code) {
+    case GDI_OK: return "ok";
+    case GDI_ERR_INVALID_ARG: return "invalid argument";
+    case GDI_ERR_NOT_SYMMETRIC: return "CSR is not symmetric";
+    case GDI_ERR_SELF_LOOP: return "self-loop";
+    case GDI_ERR_DUP_EDGE: return "duplicate edge";
+    case GDI_ERR_BAD_COLORING: return "colouring is not proper";
+    case GDI_ERR_OVERFLOW: return "integer range exceeded";
+    case GDI_ERR_OOM: return "out of memory";
+    case GDI_ERR_CUDA: return "CUDA error";
+    case GDI_ERR_TIMEOUT: return "device wait timed out";
+    case GDI_ERR_NOT_ANNEALED: return "no anneal has run";
+    case GDI_ERR_TOO_LARGE: return "problem too large for this build";
+    default: return "unknown error";
+    }
+}
+
+const char *gdi_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

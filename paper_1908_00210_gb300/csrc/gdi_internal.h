@@ -1,0 +1,60 @@
+// gdi_internal.h -- device-side data layout shared by the host API (gdi_api.cpp) and the kernels
+// (gdi_kernels.cu) of libgdi.so.  Not part of the public ABI.
+#pragma once
+
+#include <stddef.h>
+#include <stdint.h>
+
+// Rank space: every instance q is relabelled so that its vertices are sorted by (colour, id);
+// colour classes are then contiguous rank ranges [class_ptr[k], class_ptr[k+1]).  Rank-space ids
+// are global over the batch (instance q owns [node_off[q], node_off[q+1])).
+struct GdiDevProblem {
+    int32_t num_instances;
+    int32_t replicas;
+    int64_t N;                       // total vertices
+    const int64_t *node_off;         // [Q+1]
+    const int32_t *class_off;        // [Q+1] offsets into class_ptr
+    const int32_t *class_ptr;        // per instance: C_q + 1 class boundaries in local ranks
+    const int64_t *row_ptr;          // [N+1] rank-space CSR offsets
+    const uint32_t *col;             // [nnz] local neighbour rank | (weight < 0) << 31
+    const int32_t *rank_of;          // [N] original vertex -> global rank
+    int32_t A, B, W;
+    int32_t max_n;                   // largest instance
+    int32_t max_window;              // largest window (W or class size) over instances
+    int32_t max_degree;
+};
+
+// One annealing call.
+struct GdiDevRun {
+    int8_t *spins;                   // [R][N] spins in rank space
+    const uint32_t *tab;             // threshold rows (see gdi_api.cpp: build_table)
+    const int32_t *tab_off;          // [M+1] row offsets into tab
+    int32_t mode;                    // 0 Metropolis, 1 paper P_f
+    int32_t sweeps;                  // M
+    int32_t s_begin, s_end;
+    int32_t max_row;                 // longest table row
+    uint32_t key0, key1;             // Philox key = (seed low, seed high)
+    int32_t flags;
+    int32_t *raw_G, *final_G;        // [Q*R]
+    int64_t *raw_cut, *final_cut;    // [Q*R]
+    uint64_t *tr_digest;             // [Q*R][M] or null
+    int32_t *tr_G;
+    int64_t *tr_cut;
+    int32_t *err;                    // device error word (0 = ok)
+};
+
+// kernel launch wrappers (gdi_kernels.cu); return a cudaError_t as int
+int gdi_launch_init(const GdiDevProblem &P, int8_t *spins, const int8_t *init_orig, int init_kind,
+                    uint32_t key0, uint32_t key1, void *stream);
+int gdi_launch_cta_anneal(const GdiDevProblem &P, const GdiDevRun &R, int block, int grid_limit,
+                          void *stream, int *grid_used, size_t *smem_used);
+int gdi_cta_smem_bytes(const GdiDevProblem &P, const GdiDevRun &R, int block, size_t *bytes, int *hist);
+int gdi_launch_gather_spins(const GdiDevProblem &P, const int8_t *spins_rank, int8_t *out_orig,
+                            void *stream);
+
+// flags mirrored from gdi.h
+#define GDI_DEV_TRACE 1
+#define GDI_DEV_NO_REPAIR 2
+
+// device error codes written to GdiDevRun::err
+#define GDI_DEVERR_RANGE 1

@@ -1,0 +1,595 @@
+// gdi_kernels.cu -- sm_103a kernels of libgdi.so: the GDI annealing sweep (Algorithm 3 of
+// Cook, Jin, Tan, arXiv:1908.00210), its initial state, the exact-balance repair and the cut.
+//
+// CTA-resident path: one thread block anneals one (instance, replica) at a time with the whole
+// spin vector in shared memory (int8 per vertex); the rank-space CSR streams from L2/HBM.  The
+// block loops over its work items (persistent), sweeps, colour classes and windows without
+// leaving the kernel, so an anneal of M sweeps is one launch.
+//
+// Per window (a chunk of W consecutive ranks of one colour class):
+//   1. thresholds: for every spin, the local field h_i = sum_j w_ij s_j over its CSR row (Eq. 2),
+//      a Philox4x32-10 draw u_i, the largest energy change E*(u_i) that the draw accepts (binary
+//      search of the table row), and from it the flip threshold in G:
+//        s_i = +1 flips iff G >= gamma_i = ceil((B h_i + 4A - E*) / 4A)
+//        s_i = -1 flips iff G <= gamma_i = floor((E* + B h_i - 4A) / 4A)
+//      (dE = B s_i h_i + 4A (1 - s_i G), Eq. 4-6 with G counting the other spins).
+//   2. the +1 group and the -1 group of the window each see the exact running G in threshold
+//      order (Algorithm 3's atomically updated G, serialised): with d_i = G - gamma_i (+1 group) or
+//      gamma_i - G (-1 group), the k-th spin in d-descending order flips iff d_(k) >= 2k.  The
+//      number of flips K and the cut-off d* come from a shared-memory histogram of d with suffix
+//      sums; ties at d* are resolved by rank with a block prefix count.
+//   3. G changes by -2K (+1 group) or +2K (-1 group): one shared-memory update per group, the
+//      block-level analogue of the paper's atomicAdd on G.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gdi_internal.h"
+
+namespace {
+
+constexpr int32_t GAM_INF = 1 << 30;      // |threshold| sentinel: flips always / never
+constexpr int32_t ES_NONE = INT32_MIN;    // the draw accepts no energy change
+constexpr int32_t ES_ALL = INT32_MAX;     // the draw accepts every energy change
+
+// ---------------------------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds, multipliers 0xD2511F53 and
+// 0xCD9E8D57, Weyl key increments 0x9E3779B9 and 0xBB67AE85.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int i = 0; i < 10; ++i) {
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+__device__ __forceinline__ uint32_t word_of(const uint4 &v, int i)
+{
+    return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
+}
+
+// splitmix64 finaliser (Steele, Lea, Flood 2014) -- state digest only
+__device__ __forceinline__ uint64_t splitmix64_fin(uint64_t z)
+{
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ int32_t floor_div_pos(int32_t a, int32_t b)  // b > 0
+{
+    int32_t q = a / b;
+    if ((a % b) != 0 && a < 0) --q;
+    return q;
+}
+
+// E*(u): number of table entries > u for a Metropolis row (entries are thr(dE = 1..len),
+// non-increasing), i.e. the largest dE >= 0 the draw accepts.  Paper rows hold thr(-1, 0, +1).
+__device__ __forceinline__ int32_t estar_of(const uint32_t *row, int len, int mode, uint32_t u)
+{
+    if (mode == 0) {
+        int lo = 0, hi = len;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (row[mid] > u) lo = mid + 1; else hi = mid;
+        }
+        return lo;
+    }
+    if (row[0] <= u) return ES_NONE;
+    if (row[1] <= u) return -1;
+    if (row[2] <= u) return 0;
+    return ES_ALL;
+}
+
+__device__ __forceinline__ int32_t gamma_of(int sg, int32_t h, int32_t es, int32_t A, int32_t B)
+{
+    if (sg > 0) {
+        if (es == ES_NONE) return GAM_INF;
+        if (es == ES_ALL) return -GAM_INF;
+        if (A == 0) return (B * h <= es) ? -GAM_INF : GAM_INF;
+        return -floor_div_pos(-(B * h + 4 * A - es), 4 * A);     // ceil
+    }
+    if (es == ES_NONE) return -GAM_INF;
+    if (es == ES_ALL) return GAM_INF;
+    if (A == 0) return (-B * h <= es) ? GAM_INF : -GAM_INF;
+    return floor_div_pos(es + B * h - 4 * A, 4 * A);
+}
+
+// ---------------------------------------------------------------------------------------------
+// block primitives (BS threads, red: shared scratch of >= BS/32 + 1 words of T)
+template <int BS, typename T>
+__device__ __forceinline__ T block_sum(T v, T *red)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    T s = 0;
+#pragma unroll
+    for (int i = 0; i < BS / 32; ++i) s += red[i];
+    return s;
+}
+
+// exclusive scan of one int32 per thread; returns the prefix, *total gets the block sum
+template <int BS>
+__device__ __forceinline__ int32_t block_excl_scan(int32_t v, int32_t *red, int32_t *total)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+        if (lane >= o) x += y;
+    }
+    __syncthreads();
+    if (lane == 31) red[wid] = x;
+    __syncthreads();
+    int32_t base = 0, tot = 0;
+#pragma unroll
+    for (int i = 0; i < BS / 32; ++i) {
+        const int32_t r = red[i];
+        if (i < wid) base += r;
+        tot += r;
+    }
+    *total = tot;
+    return base + x - v;
+}
+
+// ---------------------------------------------------------------------------------------------
+struct Smem {
+    int8_t *sig;        // [max_n] spins of the current item, rank order
+    int8_t *s0;         // [max_window] group (sign at window start) of each window position
+    int8_t *flag;       // [max_n] repair decisions
+    int32_t *gam;       // [max_window] flip thresholds
+    int32_t *hist;      // [H] histogram of d / suffix counts
+    uint32_t *row;      // [max_row] table row of the current sweep
+    int32_t *red32;     // [BS/32 + 2]
+    int64_t *red64;     // [BS/32 + 2]
+    int32_t *G;         // running magnetisation of the item
+};
+
+// h_i = sum_j w_ij s_j over the CSR row of local rank r (Eq. 2)
+__device__ __forceinline__ int32_t local_field(const GdiDevProblem &P, int64_t base, int32_t r,
+                                               const int8_t *sig)
+{
+    const int64_t e0 = P.row_ptr[base + r], e1 = P.row_ptr[base + r + 1];
+    int32_t h = 0;
+    for (int64_t e = e0; e < e1; ++e) {
+        const uint32_t c = __ldg(P.col + e);
+        const int32_t s = sig[c & 0x7FFFFFFFu];
+        h += (c >> 31) ? -s : s;
+    }
+    return h;
+}
+
+// count of members of group grp with d >= x (exact d), block-wide
+template <int BS>
+__device__ int32_t count_ge(const Smem &S, int32_t Wn, int grp, int32_t Gc, int64_t x)
+{
+    int32_t c = 0;
+    for (int32_t p = threadIdx.x; p < Wn; p += BS) {
+        if (S.s0[p] != grp) continue;
+        const int64_t d = grp > 0 ? (int64_t)Gc - S.gam[p] : (int64_t)S.gam[p] - Gc;
+        c += (d >= x);
+    }
+    return block_sum<BS, int32_t>(c, S.red32);
+}
+
+// Decide the flips of one group of a window and apply them (see file header, step 2).
+template <int BS>
+__device__ void select_and_flip(const Smem &S, int32_t wlo, int32_t Wn, int grp, int H)
+{
+    __syncthreads();
+    const int32_t Gc = *S.G;
+    for (int32_t b = threadIdx.x; b < H; b += BS) S.hist[b] = 0;
+    __syncthreads();
+    for (int32_t p = threadIdx.x; p < Wn; p += BS) {
+        if (S.s0[p] != grp) continue;
+        const int32_t d = grp > 0 ? Gc - S.gam[p] : S.gam[p] - Gc;
+        if (d >= 0) atomicAdd(&S.hist[d < H - 1 ? d : H - 1], 1);
+    }
+    __syncthreads();
+    // suffix sums in place: hist[x] := #{members with min(d, H-1) >= x}
+    {
+        const int32_t c = (H + BS - 1) / BS;
+        const int32_t b0 = threadIdx.x * c;
+        const int32_t b1 = min(b0 + c, H);
+        int32_t loc = 0;
+        for (int32_t b = b0; b < b1; ++b) loc += S.hist[b];
+        int32_t total;
+        const int32_t before = block_excl_scan<BS>(loc, S.red32, &total);
+        int32_t run = total - before;
+        for (int32_t b = b0; b < b1; ++b) {
+            const int32_t hb = S.hist[b];
+            S.hist[b] = run;
+            run -= hb;
+        }
+    }
+    __syncthreads();
+    const int32_t n_top = S.hist[H - 1];
+    const bool safe = n_top <= (H - 1) / 2 + 1;
+    int32_t K, t;
+    int64_t dstar;
+    if (safe) {
+        int32_t cnt = 0;
+        for (int32_t k = threadIdx.x; 2 * k <= H - 1; k += BS) cnt += (S.hist[2 * k] >= k + 1);
+        K = block_sum<BS, int32_t>(cnt, S.red32);
+        if (K == 0) return;
+        int32_t cx = 0;
+        for (int32_t x = threadIdx.x; x < H; x += BS) cx += (S.hist[x] >= K);
+        dstar = block_sum<BS, int32_t>(cx, S.red32) - 1;
+        const int32_t above = (dstar + 1 <= H - 1) ? S.hist[dstar + 1] : 0;
+        t = K - above;
+    } else {
+        // exact counting passes (rare: more than H/2 members far above the running G)
+        const int32_t n0 = count_ge<BS>(S, Wn, grp, Gc, 0);
+        int32_t lo = 0, hi = n0 - 1;
+        while (lo < hi) {
+            const int32_t mid = (lo + hi + 1) >> 1;
+            if (count_ge<BS>(S, Wn, grp, Gc, 2 * (int64_t)mid) >= mid + 1) lo = mid; else hi = mid - 1;
+        }
+        K = lo + 1;
+        int64_t dl = 2 * (int64_t)(K - 1), dh = (int64_t)1 << 32;
+        while (dl < dh) {
+            const int64_t mid = (dl + dh + 1) >> 1;
+            if (count_ge<BS>(S, Wn, grp, Gc, mid) >= K) dl = mid; else dh = mid - 1;
+        }
+        dstar = dl;
+        t = K - count_ge<BS>(S, Wn, grp, Gc, dstar + 1);
+    }
+    // apply: contiguous position chunks so that the tie prefix follows rank order
+    const int32_t chunk = (Wn + BS - 1) / BS;
+    const int32_t p0 = threadIdx.x * chunk;
+    const int32_t p1 = min(p0 + chunk, Wn);
+    int32_t ties = 0;
+    for (int32_t p = p0; p < p1; ++p) {
+        if (S.s0[p] != grp) continue;
+        int64_t d = grp > 0 ? (int64_t)Gc - S.gam[p] : (int64_t)S.gam[p] - Gc;
+        if (safe && d > H - 1) d = H - 1;
+        ties += (d == dstar);
+    }
+    int32_t total;
+    int32_t idx = block_excl_scan<BS>(ties, S.red32, &total);
+    for (int32_t p = p0; p < p1; ++p) {
+        if (S.s0[p] != grp) continue;
+        int64_t d = grp > 0 ? (int64_t)Gc - S.gam[p] : (int64_t)S.gam[p] - Gc;
+        if (safe && d > H - 1) d = H - 1;
+        bool flip = d > dstar;
+        if (d == dstar) flip = (idx++ < t);
+        if (flip) S.sig[wlo + p] = (int8_t)(-grp);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *S.G = Gc - 2 * grp * K;
+}
+
+// cut of the item: (1/2) sum_i sum_j w_ij [s_i != s_j]
+template <int BS>
+__device__ int64_t item_cut(const GdiDevProblem &P, int64_t base, int32_t n, const Smem &S)
+{
+    int64_t c = 0;
+    for (int32_t r = threadIdx.x; r < n; r += BS) {
+        const int8_t sr = S.sig[r];
+        const int64_t e0 = P.row_ptr[base + r], e1 = P.row_ptr[base + r + 1];
+        for (int64_t e = e0; e < e1; ++e) {
+            const uint32_t cc = __ldg(P.col + e);
+            if (S.sig[cc & 0x7FFFFFFFu] != sr) c += (cc >> 31) ? -1 : 1;
+        }
+    }
+    return block_sum<BS, int64_t>(c, S.red64) / 2;
+}
+
+// #majority spins with repair key (s_i h_i) <= x, and with key == x (when eq != null)
+template <int BS>
+__device__ int32_t repair_count(const GdiDevProblem &P, int64_t base, int32_t n, const Smem &S,
+                                int maj, int64_t x, bool strict)
+{
+    int32_t c = 0;
+    for (int32_t r = threadIdx.x; r < n; r += BS) {
+        if (S.sig[r] != maj) continue;
+        const int64_t key = (int64_t)maj * local_field(P, base, r, S.sig);
+        c += strict ? (key < x) : (key <= x);
+    }
+    return block_sum<BS, int32_t>(c, S.red32);
+}
+
+// Exact-balance repair: flip the k majority spins with the smallest (s_i h_i, rank) keys.
+template <int BS>
+__device__ void repair(const GdiDevProblem &P, int64_t base, int32_t n, const Smem &S)
+{
+    __syncthreads();
+    const int32_t G = *S.G;
+    const int32_t target = n & 1;
+    const int32_t aG = G < 0 ? -G : G;
+    if (aG <= target) return;
+    const int32_t k = (aG - target) / 2;
+    const int maj = G > 0 ? 1 : -1;
+    // kappa = smallest key value with count(key <= kappa) >= k ; keys lie in [-deg, deg]
+    int64_t lo = -(int64_t)P.max_degree - 1, hi = (int64_t)P.max_degree + 1;
+    while (lo < hi) {
+        const int64_t mid = lo + ((hi - lo) >> 1);
+        if (repair_count<BS>(P, base, n, S, maj, mid, false) >= k) hi = mid; else lo = mid + 1;
+    }
+    const int64_t kappa = lo;
+    const int32_t less = repair_count<BS>(P, base, n, S, maj, kappa, true);
+    const int32_t t = k - less;
+    const int32_t chunk = (n + BS - 1) / BS;
+    const int32_t p0 = threadIdx.x * chunk, p1 = min(p0 + chunk, n);
+    // keys of my chunk are recomputed below before any spin of the item changes: compute flags first
+    int32_t ties = 0;
+    for (int32_t r = p0; r < p1; ++r) {
+        if (S.sig[r] != maj) continue;
+        ties += ((int64_t)maj * local_field(P, base, r, S.sig) == kappa);
+    }
+    int32_t total;
+    int32_t idx = block_excl_scan<BS>(ties, S.red32, &total);
+    // decide every flip before writing any spin (keys are defined on the pre-repair state)
+    for (int32_t r = p0; r < p1; ++r) {
+        int8_t f = 0;
+        if (S.sig[r] == maj) {
+            const int64_t key = (int64_t)maj * local_field(P, base, r, S.sig);
+            bool flip = key < kappa;
+            if (key == kappa) flip = (idx++ < t);
+            f = flip ? 1 : 0;
+        }
+        S.flag[r] = f;
+    }
+    __syncthreads();
+    for (int32_t r = threadIdx.x; r < n; r += BS)
+        if (S.flag[r]) S.sig[r] = (int8_t)(-maj);
+    __syncthreads();
+    if (threadIdx.x == 0) *S.G = G - 2 * maj * k;
+    __syncthreads();
+}
+
+template <int BS>
+__global__ void __launch_bounds__(BS) gdi_cta_anneal_kernel(GdiDevProblem P, GdiDevRun R, int H)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Smem S;
+    {
+        unsigned char *p = smem_raw;
+        S.red64 = reinterpret_cast<int64_t *>(p); p += sizeof(int64_t) * (BS / 32 + 2);
+        S.red32 = reinterpret_cast<int32_t *>(p); p += sizeof(int32_t) * (BS / 32 + 2);
+        S.G = reinterpret_cast<int32_t *>(p); p += 16;
+        S.hist = reinterpret_cast<int32_t *>(p); p += sizeof(int32_t) * H;
+        S.gam = reinterpret_cast<int32_t *>(p); p += sizeof(int32_t) * ((P.max_window + 3) & ~3);
+        S.row = reinterpret_cast<uint32_t *>(p); p += sizeof(uint32_t) * ((R.max_row + 3) & ~3);
+        S.s0 = reinterpret_cast<int8_t *>(p); p += (P.max_window + 15) & ~15;
+        S.sig = reinterpret_cast<int8_t *>(p); p += (P.max_n + 15) & ~15;
+        S.flag = reinterpret_cast<int8_t *>(p);
+    }
+    const int32_t items = P.num_instances * P.replicas;
+    for (int32_t item = blockIdx.x; item < items; item += gridDim.x) {
+        const int32_t q = item / P.replicas;
+        const int32_t rep = item - q * P.replicas;
+        const int64_t base = P.node_off[q];
+        const int32_t n = (int32_t)(P.node_off[q + 1] - base);
+        const int32_t *cls = P.class_ptr + P.class_off[q];
+        const int32_t ncls = P.class_off[q + 1] - P.class_off[q] - 1;
+        int8_t *gsig = R.spins + (int64_t)rep * P.N + base;
+
+        int32_t g = 0;
+        for (int32_t r = threadIdx.x; r < n; r += BS) {
+            const int8_t s = gsig[r];
+            S.sig[r] = s;
+            g += s;
+        }
+        g = block_sum<BS, int32_t>(g, S.red32);
+        if (threadIdx.x == 0) *S.G = g;
+        __syncthreads();
+
+        for (int32_t sw = R.s_begin; sw < R.s_end; ++sw) {
+            const int32_t roff = R.tab_off[sw];
+            const int32_t rlen = R.tab_off[sw + 1] - roff;
+            for (int32_t k = threadIdx.x; k < rlen; k += BS) S.row[k] = R.tab[roff + k];
+            __syncthreads();
+            for (int32_t c = 0; c < ncls; ++c) {
+                const int32_t clo = cls[c], chi = cls[c + 1];
+                const int32_t Wn0 = P.W > 0 ? P.W : (chi - clo);
+                for (int32_t wlo = clo; wlo < chi; wlo += Wn0) {
+                    const int32_t whi = min(wlo + Wn0, chi);
+                    const int32_t Wn = whi - wlo;
+                    // step 1: thresholds, one Philox call per aligned quad of ranks
+                    const int32_t q0 = wlo >> 2, q1 = (whi - 1) >> 2;
+                    for (int32_t qd = q0 + threadIdx.x; qd <= q1; qd += BS) {
+                        const uint4 u4 = philox4x32_10(
+                            make_uint4((uint32_t)qd, (uint32_t)sw, (uint32_t)q, (uint32_t)rep),
+                            R.key0, R.key1);
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            const int32_t r = 4 * qd + j;
+                            if (r < wlo || r >= whi) continue;
+                            const int sg = S.sig[r];
+                            const int32_t h = local_field(P, base, r, S.sig);
+                            const int32_t es = estar_of(S.row, rlen, R.mode, word_of(u4, j));
+                            S.gam[r - wlo] = gamma_of(sg, h, es, P.A, P.B);
+                            S.s0[r - wlo] = (int8_t)sg;
+                        }
+                    }
+                    // step 2/3: the two groups in the canonical order (+1 first on even sweeps)
+                    const int first = (sw & 1) ? -1 : 1;
+                    select_and_flip<BS>(S, wlo, Wn, first, H);
+                    select_and_flip<BS>(S, wlo, Wn, -first, H);
+                    __syncthreads();
+                }
+            }
+            if (R.flags & GDI_DEV_TRACE) {
+                uint64_t dg = 0;
+                for (int32_t r = threadIdx.x; r < n; r += BS)
+                    if (S.sig[r] > 0)
+                        dg += splitmix64_fin((uint64_t)(uint32_t)r | ((uint64_t)(sw & 0xFFFF) << 32) |
+                                             ((uint64_t)(rep & 0xFFFF) << 48));
+                dg = block_sum<BS, uint64_t>(dg, reinterpret_cast<uint64_t *>(S.red64));
+                const int64_t ct = item_cut<BS>(P, base, n, S);
+                if (threadIdx.x == 0) {
+                    const int64_t o = (int64_t)item * R.sweeps + sw;
+                    R.tr_digest[o] = dg;
+                    R.tr_G[o] = *S.G;
+                    R.tr_cut[o] = ct;
+                }
+            }
+            __syncthreads();
+        }
+        // outputs before and after the exact-balance repair
+        const int64_t raw_cut = item_cut<BS>(P, base, n, S);
+        __syncthreads();
+        const int32_t raw_G = *S.G;
+        if (!(R.flags & GDI_DEV_NO_REPAIR)) repair<BS>(P, base, n, S);
+        const int64_t fin_cut = item_cut<BS>(P, base, n, S);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            R.raw_G[item] = raw_G;
+            R.raw_cut[item] = raw_cut;
+            R.final_G[item] = *S.G;
+            R.final_cut[item] = fin_cut;
+        }
+        for (int32_t r = threadIdx.x; r < n; r += BS) gsig[r] = S.sig[r];
+        __syncthreads();
+    }
+}
+
+// Initial state (Alg. 3 "initialize all s_i"): balanced random pairs from Philox, or the caller's
+// spins scattered from original order to rank order.
+__global__ void gdi_init_kernel(GdiDevProblem P, int8_t *spins, const int8_t *init_orig, int kind,
+                                uint32_t key0, uint32_t key1)
+{
+    const int64_t total = (int64_t)P.replicas * P.N;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t rep = (int32_t)(t / P.N);
+        const int64_t v = t - (int64_t)rep * P.N;
+        if (kind == 1) {            // caller spins, original vertex v
+            spins[(int64_t)rep * P.N + P.rank_of[v]] = init_orig[t] > 0 ? 1 : -1;
+            continue;
+        }
+        // random: v is a global rank; find its instance by binary search of node_off
+        int32_t lo = 0, hi = P.num_instances - 1;
+        while (lo < hi) {
+            const int32_t mid = (lo + hi + 1) >> 1;
+            if (P.node_off[mid] <= v) lo = mid; else hi = mid - 1;
+        }
+        const int64_t base = P.node_off[lo];
+        const int32_t n = (int32_t)(P.node_off[lo + 1] - base);
+        const int32_t r = (int32_t)(v - base);
+        int8_t s;
+        if ((n & 1) && r == n - 1) {
+            s = -1;
+        } else {
+            const int32_t pr = r >> 1;
+            const uint4 u4 = philox4x32_10(make_uint4((uint32_t)(pr >> 2), 0xFFFFFFFFu, (uint32_t)lo,
+                                                      (uint32_t)rep), key0, key1);
+            const int8_t a = (word_of(u4, pr & 3) >> 31) ? -1 : 1;
+            s = (r & 1) ? (int8_t)-a : a;
+        }
+        spins[t] = s;
+    }
+}
+
+__global__ void gdi_gather_kernel(GdiDevProblem P, const int8_t *spins, int8_t *out)
+{
+    const int64_t total = (int64_t)P.replicas * P.N;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t rep = (int32_t)(t / P.N);
+        const int64_t v = t - (int64_t)rep * P.N;
+        out[t] = spins[(int64_t)rep * P.N + P.rank_of[v]];
+    }
+}
+
+size_t cta_smem(const GdiDevProblem &P, const GdiDevRun &R, int BS, int H)
+{
+    size_t b = sizeof(int64_t) * (BS / 32 + 2) + sizeof(int32_t) * (BS / 32 + 2) + 16;
+    b += sizeof(int32_t) * (size_t)H;
+    b += sizeof(int32_t) * (size_t)((P.max_window + 3) & ~3);
+    b += sizeof(uint32_t) * (size_t)((R.max_row + 3) & ~3);
+    b += (size_t)((P.max_window + 15) & ~15);
+    b += (size_t)((P.max_n + 15) & ~15);
+    b += (size_t)P.max_n;
+    return b;
+}
+
+int hist_bins(const GdiDevProblem &P)
+{
+    int H = 64;
+    while (H < 2 * P.max_window + 2 && H < 4096) H <<= 1;
+    return H;
+}
+
+template <int BS>
+int launch_cta(const GdiDevProblem &P, const GdiDevRun &R, int grid_limit, cudaStream_t st,
+               int *grid_used, size_t *smem_used)
+{
+    const int H = hist_bins(P);
+    const size_t smem = cta_smem(P, R, BS, H);
+    cudaError_t e = cudaFuncSetAttribute(gdi_cta_anneal_kernel<BS>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return (int)e;
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gdi_cta_anneal_kernel<BS>, BS, smem);
+    if (e != cudaSuccess) return (int)e;
+    if (per_sm < 1) return (int)cudaErrorInvalidConfiguration;
+    const int items = P.num_instances * P.replicas;
+    int grid = sms * per_sm;
+    if (grid > items) grid = items;
+    if (grid_limit > 0 && grid > grid_limit) grid = grid_limit;
+    gdi_cta_anneal_kernel<BS><<<grid, BS, smem, st>>>(P, R, H);
+    if (grid_used) *grid_used = grid;
+    if (smem_used) *smem_used = smem;
+    return (int)cudaGetLastError();
+}
+
+}  // namespace
+
+int gdi_cta_smem_bytes(const GdiDevProblem &P, const GdiDevRun &R, int block, size_t *bytes, int *hist)
+{
+    const int H = hist_bins(P);
+    if (hist) *hist = H;
+    if (bytes) *bytes = cta_smem(P, R, block, H);
+    return 0;
+}
+
+int gdi_launch_cta_anneal(const GdiDevProblem &P, const GdiDevRun &R, int block, int grid_limit,
+                          void *stream, int *grid_used, size_t *smem_used)
+{
+    cudaStream_t st = (cudaStream_t)stream;
+    switch (block) {
+    case 128: return launch_cta<128>(P, R, grid_limit, st, grid_used, smem_used);
+    case 256: return launch_cta<256>(P, R, grid_limit, st, grid_used, smem_used);
+    case 512: return launch_cta<512>(P, R, grid_limit, st, grid_used, smem_used);
+    case 1024: return launch_cta<1024>(P, R, grid_limit, st, grid_used, smem_used);
+    default: return (int)cudaErrorInvalidValue;
+    }
+}
+
+int gdi_launch_init(const GdiDevProblem &P, int8_t *spins, const int8_t *init_orig, int init_kind,
+                    uint32_t key0, uint32_t key1, void *stream)
+{
+    const int64_t total = (int64_t)P.replicas * P.N;
+    int grid = (int)((total + 255) / 256);
+    if (grid > 152 * 32) grid = 152 * 32;
+    if (grid < 1) grid = 1;
+    gdi_init_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(P, spins, init_orig, init_kind, key0, key1);
+    return (int)cudaGetLastError();
+}
+
+int gdi_launch_gather_spins(const GdiDevProblem &P, const int8_t *spins_rank, int8_t *out_orig,
+                            void *stream)
+{
+    const int64_t total = (int64_t)P.replicas * P.N;
+    int grid = (int)((total + 255) / 256);
+    if (grid > 152 * 32) grid = 152 * 32;
+    if (grid < 1) grid = 1;
+    gdi_gather_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(P, spins_rank, out_orig);
+    return (int)cudaGetLastError();
+}
