@@ -259,9 +259,11 @@ def run_ours(args, wl, rank, world, local):
     # end to end through the public API with host buffers: create from the host CSR (upload),
     # anneal, read spins and results back (host pinned staging for the spins)
     e2e_ms = []
+    if args.quick:
+        e2e_ms = [float("nan")]
     h2d = g.row_ptr.nbytes + g.col.nbytes + g.w.nbytes + (g.color.nbytes if g.color is not None else 0)
     d2h = wl["replicas"] * g.n + 24 * wl["replicas"]
-    for _ in range(max(1, min(args.steps, 3))):
+    for _ in range(0 if args.quick else max(1, min(args.steps, 3))):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         a2 = P.Annealer(g, A=wl["A"], B=wl["B"], W=wl["W"], replicas=wl["replicas"])
@@ -282,6 +284,8 @@ def run_ours(args, wl, rank, world, local):
     alu_peak = dev_props.multi_processor_count * 128 * sm_max * 1e6 / 1e12   # Tops/s
     achieved = ops_per_update * (updates / (ms_per_step / 1e3)) / 1e12
     try:
+        if args.quick:
+            raise RuntimeError("skipped (--quick)")
         cpu_v, cores, sample = oracle_throughput(g, wl, seconds=12.0)
         cpu = {"value": cpu_v, "unit": "spin-updates/s", "cores": cores, "kind": "oracle", "sample": sample}
     except Exception as ex:  # the baseline is reported, not required
@@ -320,8 +324,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--sweeps", type=int, default=0,
+                    help="profiling only: override the workload's sweep count")
+    ap.add_argument("--quick", action="store_true",
+                    help="profiling only: skip the CPU baseline and the end-to-end leg")
     args = ap.parse_args()
-    wl = WORKLOADS[args.workload]
+    wl = dict(WORKLOADS[args.workload])
+    if args.sweeps > 0:
+        wl["sweeps"] = args.sweeps
     rank, world, local = dist_setup(args.gpus)
     if args.impl == "reference":
         run_reference(args, wl, rank, world)
