@@ -29,18 +29,26 @@ import numpy as np  # noqa: E402
 # ---------------------------------------------------------------------------------------------
 # Workloads (synthetic stand-ins for the paper's G-set graphs; see the design doc for the recipes)
 WORKLOADS = {
+    # Barabasi-Albert n = 10^6, m = 5, unit weights, greedy colouring (6 classes), 8 replicas,
+    # 500 sweeps, window W = 256: the grid-scale path (every SM on one graph)
+    "ba1m_r8": dict(kind="ba", n=1_000_000, m=5, gseed=4004, A=1, B=4, W=256, replicas=8,
+                    sweeps=500, t0=12.0, t1=0.2, seed=1,
+                    roofline=dict(bound="hbm", bytes_per_update=56)),
     # 2-D torus 100 x 100, +-1 weights, checkerboard colouring, 64 replicas, 5000 sweeps
     "torus100_r64": dict(kind="torus", L=100, gseed=2002, A=1, B=4, W=1024, replicas=64,
-                         sweeps=5000, t0=12.0, t1=0.2, seed=1),
+                         sweeps=5000, t0=12.0, t1=0.2, seed=1,
+                         roofline=dict(bound="alu", ops_per_update=100)),
     # Erdos-Renyi n = 800, p = 0.06, unit weights, greedy colouring, 1000 sweeps, 1 replica
     "er800": dict(kind="er", n=800, p=0.06, gseed=1001, A=1, B=4, W=64, replicas=1, sweeps=1000,
-                  t0=12.0, t1=0.2, seed=1),
+                  t0=12.0, t1=0.2, seed=1, roofline=dict(bound="alu", ops_per_update=300)),
 }
-DEFAULT_WORKLOAD = "torus100_r64"
+DEFAULT_WORKLOAD = "ba1m_r8"
 
 
 def make_graph(wl):
-    from gdi_synth import erdos_renyi, torus2d
+    from gdi_synth import barabasi_albert, erdos_renyi, torus2d
+    if wl["kind"] == "ba":
+        return barabasi_albert(wl["n"], wl["m"], wl["gseed"])
     if wl["kind"] == "torus":
         return torus2d(wl["L"], wl["gseed"], signed=True)
     if wl["kind"] == "er":
@@ -218,7 +226,9 @@ def run_ours(args, wl, rank, world, local):
     stream = torch.cuda.Stream()
     seed = wl["seed"] + 7919 * rank
     sch = P.Schedule(sweeps=wl["sweeps"], t0=wl["t0"], t1=wl["t1"])
+    t_create = time.perf_counter()
     ann = P.Annealer(g, A=wl["A"], B=wl["B"], W=wl["W"], replicas=wl["replicas"])
+    create_s = time.perf_counter() - t_create
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")
     updates = wl["replicas"] * wl["sweeps"] * g.n
 
@@ -226,6 +236,7 @@ def run_ours(args, wl, rank, world, local):
         for _ in range(args.warmup):
             ann.anneal(sch, seed, stream=stream)
             ann.results()
+    launch_path = ann.last_launch()["path"] if args.warmup > 0 else 0
     torch.cuda.synchronize()
     barrier(world)
     torch.cuda.synchronize()
@@ -240,9 +251,9 @@ def run_ours(args, wl, rank, world, local):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            ann.anneal(sch, seed, stream=stream)        # init kernel + anneal kernel
+            ann.anneal(sch, seed, stream=stream)
             e1.record(stream)
-            launches += 2
+            launches += launches_per_anneal(launch_path, wl["replicas"])
             e1.synchronize()
             ms.append(e0.elapsed_time(e1))
     torch.cuda.synchronize()
@@ -251,38 +262,54 @@ def run_ours(args, wl, rank, world, local):
     wall = time.perf_counter() - wall0
     clk = clocks.stop()
     res = ann.results()
+    launch = ann.last_launch()
     total_ms = sum(ms)
     total_ms = allreduce_max(total_ms, world)
     ms_per_step = total_ms / args.steps
     value = world * updates / (ms_per_step / 1e3)
 
-    # end to end through the public API with host buffers: create from the host CSR (upload),
-    # anneal, read spins and results back (host pinned staging for the spins)
+    # end to end through the public API with host buffers: the step's input (balanced initial spins
+    # of every replica) is copied from pinned host memory, the spins and results are read back
+    rng = np.random.default_rng(1234 + rank)
+    init_t = torch.empty((wl["replicas"], g.n), dtype=torch.int8, pin_memory=True)
+    init_np = init_t.numpy()
+    half = np.ones(g.n, dtype=np.int8)
+    half[g.n // 2:] = -1
+    for r in range(wl["replicas"]):
+        init_np[r] = rng.permutation(half)
     e2e_ms = []
-    if args.quick:
-        e2e_ms = [float("nan")]
-    h2d = g.row_ptr.nbytes + g.col.nbytes + g.w.nbytes + (g.color.nbytes if g.color is not None else 0)
+    h2d = init_np.nbytes
     d2h = wl["replicas"] * g.n + 24 * wl["replicas"]
     for _ in range(0 if args.quick else max(1, min(args.steps, 3))):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        a2 = P.Annealer(g, A=wl["A"], B=wl["B"], W=wl["W"], replicas=wl["replicas"])
-        a2.anneal(sch, seed, stream=stream)
-        a2.spins()
-        a2.results()
+        ann.anneal(sch, seed, init=init_np, stream=stream)
+        ann.spins()
+        ann.results()
         e2e_ms.append(1e3 * (time.perf_counter() - t0))
-        a2.close()
+    if not e2e_ms:
+        e2e_ms = [float("nan")]
     e2e_value = world * updates / (statistics.median(e2e_ms) / 1e3)
 
     if rank != 0:
         return
     pk = peaks()
-    # roofline: the anneal is bound by integer issue (Philox, field gather from shared memory,
-    # threshold search and the window selection); see the design doc for the op count and the peak
-    ops_per_update = ALU_OPS_PER_UPDATE.get(args.workload, 100)
-    sm_max = float(pk.get("sm_max_mhz", 2070.0))
-    alu_peak = dev_props.multi_processor_count * 128 * sm_max * 1e6 / 1e12   # Tops/s
-    achieved = ops_per_update * (updates / (ms_per_step / 1e3)) / 1e12
+    rf = wl["roofline"]
+    rate = updates / (ms_per_step / 1e3)
+    if rf["bound"] == "hbm":
+        peak = float(pk.get("hbm_gbs", 6800.0))
+        achieved = rf["bytes_per_update"] * rate / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None,
+                "bytes_per_update": rf["bytes_per_update"],
+                "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
+    else:
+        sm_max = float(pk.get("sm_max_mhz", 2070.0))
+        peak = dev_props.multi_processor_count * 128 * sm_max * 1e6 / 1e12
+        achieved = rf["ops_per_update"] * rate / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
+                "frac": achieved / peak, "traffic": None, "ops_per_update": rf["ops_per_update"],
+                "peak_note": "SMs x 128 int32 lanes x max SM clock (derived, see DESIGN.md)"}
     try:
         if args.quick:
             raise RuntimeError("skipped (--quick)")
@@ -296,15 +323,14 @@ def run_ours(args, wl, rank, world, local):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
         "data": "synthetic", "config": config_of(args.workload, wl, g),
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s",
-                     "frac": achieved / alu_peak, "traffic": None,
-                     "ops_per_update": ops_per_update,
-                     "peak_note": "152 SMs x 128 int32 lanes x max SM clock (derived, see DESIGN.md)"},
+        "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": "spin-updates/s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
         "clocks": clk, "gpu_launches": launches,
         "wall_s_timed_region": wall,
+        "launch": launch,
+        "create_s": create_s,
         "result": {"final_cut_median": float(np.median(res["final_cut"])),
                    "final_G_max_abs": int(np.abs(res["final_G"]).max()),
                    "raw_G_max_abs": int(np.abs(res["raw_G"]).max())},
@@ -313,8 +339,13 @@ def run_ours(args, wl, rank, world, local):
     ann.close()
 
 
-# integer operations per spin update counted from the kernel source ("Roofline")
-ALU_OPS_PER_UPDATE = {"torus100_r64": 100, "er800": 300}
+
+# kernels of ours per gdi_anneal: CTA path = init + anneal; grid path = init + (pack + anneal +
+# unpack) per 8-replica group + raw cut + repair (hist, select, ties, mark, apply) + final cut
+def launches_per_anneal(path: int, replicas: int) -> int:
+    if path == 2:
+        return 1 + 3 * ((replicas + 7) // 8) + 1 + 5 + 1
+    return 2
 
 
 def main():

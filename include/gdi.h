@@ -51,6 +51,11 @@ extern "C" {
 #define GDI_METROPOLIS 0   /* accept with min(1, exp(-dE/T_s)), T_s geometric from t0 to t1          */
 #define GDI_PAPER_PF   1   /* Alg. 2/3: argmin, then flip with probability P_f; P_f geometric pf0->pf1 */
 
+/* kernel paths (gdi_configure) */
+#define GDI_PATH_AUTO 0   /* CTA-resident unless a single instance has more than 32768 vertices  */
+#define GDI_PATH_CTA  1   /* one thread block anneals one (instance, replica), spins in shared memory */
+#define GDI_PATH_GRID 2   /* one instance over every SM (needs W >= 1); up to 8 replicas per pass  */
+
 /* gdi_run.flags */
 #define GDI_FLAG_TRACE     1  /* record per-sweep G, cut and state digest (slower; for parity)     */
 #define GDI_FLAG_NO_REPAIR 2  /* skip the exact-balance repair after the last sweep                */
@@ -134,6 +139,16 @@ int gdi_balance(gdi_ctx *ctx, int32_t instance, int32_t replica, int32_t *raw_G,
  * digest = sum over ranks i with s_i = +1 of splitmix64(i | sweep << 32 | replica << 48) mod 2^64.
  * Any pointer may be NULL.  Host pointers. */
 int gdi_get_trace(gdi_ctx *ctx, uint64_t *digest, int32_t *G, int64_t *cut);
+
+/* Launch configuration of later gdi_anneal calls: kernel path (GDI_PATH_*), threads per block of
+ * the CTA-resident path (0 = keep, else 128/256/512/1024) and a cap on the number of blocks
+ * (0 = one wave on every SM).  Results do not depend on any of these (the autotuner relies on it). */
+int gdi_configure(gdi_ctx *ctx, int32_t path, int32_t block, int32_t grid_limit);
+
+/* What the last gdi_anneal launched: path, blocks, dynamic shared memory per block, and how many
+ * times the grid-scale path took its exact fallback (0 on the CTA path).  Synchronises. */
+int gdi_last_launch(gdi_ctx *ctx, int32_t *path, int32_t *grid, int64_t *smem_bytes,
+                    int32_t *fallbacks);
 
 /* Context facts: number of colour classes per instance (host [num_instances], may be NULL),
  * the largest degree, and the E_cap of the last schedule (0 before any anneal). */

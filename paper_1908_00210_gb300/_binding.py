@@ -26,7 +26,9 @@ ERRORS = {
 
 # every entry point that include/gdi.h declares
 EXPORTS = ["gdi_create", "gdi_anneal", "gdi_get_spins", "gdi_get_results", "gdi_cut", "gdi_balance",
-           "gdi_get_trace", "gdi_info", "gdi_destroy", "gdi_strerror", "gdi_last_error"]
+           "gdi_get_trace", "gdi_configure", "gdi_last_launch", "gdi_info", "gdi_destroy",
+           "gdi_strerror", "gdi_last_error"]
+GDI_PATH_AUTO, GDI_PATH_CTA, GDI_PATH_GRID = 0, 1, 2
 
 
 class GdiError(RuntimeError):
@@ -76,6 +78,8 @@ def load():
     L.gdi_balance.argtypes = [vp, i32, i32, vp, vp]
     L.gdi_get_trace.argtypes = [vp, vp, vp, vp]
     L.gdi_info.argtypes = [vp, vp, vp, vp]
+    L.gdi_configure.argtypes = [vp, i32, i32, i32]
+    L.gdi_last_launch.argtypes = [vp, vp, vp, vp, vp]
     L.gdi_destroy.argtypes = [vp]
     L.gdi_destroy.restype = None
     L.gdi_strerror.argtypes = [C.c_int]
@@ -209,6 +213,18 @@ class Annealer:
         c = np.empty((k, self.sweeps), np.int64)
         _check(load().gdi_get_trace(self._h, d.ctypes.data, g.ctypes.data, c.ctypes.data))
         return d, g, c
+
+    def configure(self, path: int = GDI_PATH_AUTO, block: int = 0, grid_limit: int = 0):
+        _check(load().gdi_configure(self._h, path, block, grid_limit))
+        return self
+
+    def last_launch(self):
+        pa = np.zeros(1, np.int32)
+        gr = np.zeros(1, np.int32)
+        sm = np.zeros(1, np.int64)
+        fb = np.zeros(1, np.int32)
+        _check(load().gdi_last_launch(self._h, pa.ctypes.data, gr.ctypes.data, sm.ctypes.data, fb.ctypes.data))
+        return dict(path=int(pa[0]), grid=int(gr[0]), smem=int(sm[0]), fallbacks=int(fb[0]))
 
     def info(self):
         nc = np.zeros(self.num_instances, np.int32)

@@ -59,7 +59,13 @@ struct gdi_ctx {
     int device = 0;
     int32_t Q = 0, R = 1, A = 0, B = 1, W = 0;
     int64_t N = 0, nnz = 0;
-    int32_t max_n = 0, max_window = 0, max_degree = 0;
+    int32_t max_n = 0, max_window = 0, max_degree = 0, max_class = 0;
+    int32_t path = 0;                        // GDI_PATH_*
+    DevBuf<uint8_t> g_packed, g_rflags;
+    DevBuf<int16_t> g_tables;
+    DevBuf<int32_t> g_gin, g_Gcls, g_err, g_status, g_rhist, g_rties, g_rparams;
+    DevBuf<unsigned int> g_bar;
+    bool used_grid = false;
     std::vector<int32_t> num_classes;       // per instance
     DevBuf<int64_t> node_off, row_ptr;
     DevBuf<int32_t> class_off, class_ptr, rank_of;
@@ -67,6 +73,7 @@ struct gdi_ctx {
     DevBuf<int8_t> spins, init_stage, out_stage;
     DevBuf<uint32_t> tab;
     DevBuf<int32_t> tab_off;
+    DevBuf<float> temp;
     DevBuf<int32_t> raw_G, final_G, tr_G, err;
     DevBuf<int64_t> raw_cut, final_cut, tr_cut;
     DevBuf<uint64_t> tr_digest;
@@ -96,14 +103,34 @@ struct gdi_ctx {
         P.max_n = max_n;
         P.max_window = max_window;
         P.max_degree = max_degree;
+        P.max_class = max_class;
         return P;
     }
     void release()
     {
         node_off.release(); row_ptr.release(); class_off.release(); class_ptr.release();
         rank_of.release(); col.release(); spins.release(); init_stage.release(); out_stage.release();
-        tab.release(); tab_off.release(); raw_G.release(); final_G.release(); tr_G.release();
+        tab.release(); tab_off.release(); temp.release(); raw_G.release(); final_G.release(); tr_G.release();
         err.release(); raw_cut.release(); final_cut.release(); tr_cut.release(); tr_digest.release();
+        g_packed.release(); g_rflags.release(); g_tables.release(); g_gin.release(); g_Gcls.release();
+        g_err.release(); g_status.release(); g_rhist.release(); g_rties.release(); g_rparams.release();
+        g_bar.release();
+    }
+    GdiGridScratch grid_scratch()
+    {
+        GdiGridScratch X;
+        X.packed = g_packed.p;
+        X.tables = g_tables.p;
+        X.gin = g_gin.p;
+        X.Gcls = g_Gcls.p;
+        X.bar = g_bar.p;
+        X.err = g_err.p;
+        X.status = g_status.p;
+        X.rhist = g_rhist.p;
+        X.rflags = g_rflags.p;
+        X.rties = g_rties.p;
+        X.rparams = g_rparams.p;
+        return X;
     }
 };
 
@@ -121,11 +148,12 @@ double sched_at(double v0, double v1, int s, int M)
 }
 
 int build_table(const gdi_schedule &S, std::vector<uint32_t> &tab, std::vector<int32_t> &off,
-                int32_t &ecap, int32_t &max_row)
+                std::vector<float> &temp, int32_t &ecap, int32_t &max_row)
 {
     const int M = S.sweeps;
     tab.clear();
     off.assign((size_t)M + 1, 0);
+    temp.assign((size_t)M, 0.f);
     max_row = 0;
     if (S.mode == GDI_METROPOLIS) {
         if (!(S.t0 > 0.0) || !(S.t1 > 0.0) || !std::isfinite(S.t0) || !std::isfinite(S.t1))
@@ -133,6 +161,7 @@ int build_table(const gdi_schedule &S, std::vector<uint32_t> &tab, std::vector<i
         for (int s = 0; s < M; ++s) {
             off[s] = (int32_t)tab.size();
             const double T = sched_at(S.t0, S.t1, s, M);
+            temp[(size_t)s] = (float)T;
             for (int64_t E = 1;; ++E) {
                 const double t = std::floor(std::exp(-(double)E / T) * 4294967296.0);
                 if (t <= 0.0) break;
@@ -322,6 +351,7 @@ int gdi_create(gdi_ctx **out, const gdi_graph *g, const gdi_model *m)
                 class_ptr.push_back(cnt[(size_t)k]);
                 const int32_t sz = cnt[(size_t)k + 1] - cnt[(size_t)k];
                 c->max_window = std::max(c->max_window, m->W > 0 ? std::min(m->W, sz) : sz);
+                c->max_class = std::max(c->max_class, sz);
                 ++nclass;
             }
         }
@@ -406,8 +436,9 @@ int gdi_anneal(gdi_ctx *c, const gdi_schedule *S, const gdi_run *run)
 
     std::vector<uint32_t> tab;
     std::vector<int32_t> off;
+    std::vector<float> temp;
     int32_t ecap = 0, max_row = 0;
-    int rc = build_table(*S, tab, off, ecap, max_row);
+    int rc = build_table(*S, tab, off, temp, ecap, max_row);
     if (rc) return rc;
     // integer ranges: |B h + 4A - E*| and |G| must stay far below the 2^30 threshold sentinels
     if ((int64_t)c->B * c->max_degree + 4LL * c->A + ecap >= ((int64_t)1 << 29))
@@ -416,11 +447,14 @@ int gdi_anneal(gdi_ctx *c, const gdi_schedule *S, const gdi_run *run)
     cudaStream_t st = (cudaStream_t)run->stream;
     cudaError_t e = c->tab.alloc(tab.size());
     if (e == cudaSuccess) e = c->tab_off.alloc(off.size());
+    if (e == cudaSuccess) e = c->temp.alloc(temp.size());
     if (e != cudaSuccess) return fail(GDI_ERR_OOM, "device allocation failed (table)");
     // pageable source: the copy is staged before cudaMemcpyAsync returns
     e = cudaMemcpyAsync(c->tab.p, tab.data(), tab.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(c->tab_off.p, off.data(), off.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->temp.p, temp.data(), temp.size() * sizeof(float), cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return cuda_fail(e, "table upload");
 
     const bool trace = (run->flags & GDI_FLAG_TRACE) != 0;
@@ -458,6 +492,7 @@ int gdi_anneal(gdi_ctx *c, const gdi_schedule *S, const gdi_run *run)
     R.spins = c->spins.p;
     R.tab = c->tab.p;
     R.tab_off = c->tab_off.p;
+    R.temp = c->temp.p;
     R.mode = S->mode;
     R.sweeps = S->sweeps;
     R.s_begin = s_begin;
@@ -478,14 +513,55 @@ int gdi_anneal(gdi_ctx *c, const gdi_schedule *S, const gdi_run *run)
     size_t need = 0;
     int H = 0;
     gdi_cta_smem_bytes(P, R, c->block, &need, &H);
-    int max_optin = 0;
+    int max_optin = 0, sms = 0;
     cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
-    if (need > (size_t)max_optin)
-        return fail(GDI_ERR_TOO_LARGE, "instance needs " + std::to_string(need) +
-                                           " bytes of shared memory per block (limit " +
-                                           std::to_string(max_optin) + ")");
-    int ke = gdi_launch_cta_anneal(P, R, c->block, c->grid_limit, st, &c->last_grid, &c->last_smem);
-    if (ke) return cuda_fail((cudaError_t)ke, "anneal kernel launch");
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+    bool grid = false;
+    if (c->path == GDI_PATH_GRID) grid = true;
+    else if (c->path == GDI_PATH_AUTO) grid = (c->Q == 1 && (c->max_n > 32768 || need > (size_t)max_optin));
+    if (!grid) {
+        if (need > (size_t)max_optin)
+            return fail(GDI_ERR_TOO_LARGE, "instance needs " + std::to_string(need) +
+                                               " bytes of shared memory per block (limit " +
+                                               std::to_string(max_optin) + "); use one instance with W > 0");
+        int ke = gdi_launch_cta_anneal(P, R, c->block, c->grid_limit, st, &c->last_grid, &c->last_smem);
+        if (ke) return cuda_fail((cudaError_t)ke, "anneal kernel launch");
+        c->used_grid = false;
+    } else {
+        if (c->Q != 1 || c->W < 1)
+            return fail(GDI_ERR_TOO_LARGE, "the grid-scale path anneals one instance with a window W >= 1");
+        if (c->max_degree > 32767) return fail(GDI_ERR_TOO_LARGE, "degree above 32767 on the grid-scale path");
+        int spc = 0, wpc = 0;
+        size_t smem = 0;
+        const int nblk = c->grid_limit > 0 ? std::min(c->grid_limit, sms) : sms;
+        if (gdi_grid_plan(P, max_row, nblk, &spc, &wpc, &smem) != 0 || smem > (size_t)max_optin ||
+            !gdi_grid_fallback_fits(spc))
+            return fail(GDI_ERR_TOO_LARGE, "grid-scale plan needs " + std::to_string(smem) +
+                                               " bytes of shared memory per block; use a smaller W");
+        const int D = c->max_degree;
+        e = c->g_packed.alloc((size_t)c->N);
+        if (e == cudaSuccess) e = c->g_rflags.alloc((size_t)c->N);
+        if (e == cudaSuccess) e = c->g_tables.alloc((size_t)nblk * 8 * GDI_GRID_TW);
+        if (e == cudaSuccess) e = c->g_gin.alloc((size_t)nblk * 8);
+        if (e == cudaSuccess) e = c->g_Gcls.alloc(8);
+        if (e == cudaSuccess) e = c->g_err.alloc(4);
+        if (e == cudaSuccess) e = c->g_status.alloc(16);
+        if (e == cudaSuccess) e = c->g_rhist.alloc((size_t)8 * (2 * D + 1));
+        if (e == cudaSuccess) e = c->g_rties.alloc((size_t)8 * 152 * 4);
+        if (e == cudaSuccess) e = c->g_rparams.alloc(32);
+        if (e == cudaSuccess) e = c->g_bar.alloc(2);
+        if (e != cudaSuccess) return fail(GDI_ERR_OOM, "device allocation failed (grid scratch)");
+        cudaMemsetAsync(c->g_err.p, 0, sizeof(int32_t), st);
+        cudaMemsetAsync(c->g_status.p, 0, 16 * sizeof(int32_t), st);
+        const GdiGridScratch X = c->grid_scratch();
+        int ke = gdi_launch_grid_anneal(P, R, X, c->spins.p, nblk, spc, wpc, smem, st);
+        if (ke) return cuda_fail((cudaError_t)ke, "grid anneal launch");
+        ke = gdi_launch_grid_finish(P, R, X, c->spins.p, (run->flags & GDI_FLAG_NO_REPAIR) ? 0 : 1, st);
+        if (ke) return cuda_fail((cudaError_t)ke, "grid finish kernels");
+        c->used_grid = true;
+        c->last_grid = nblk;
+        c->last_smem = smem;
+    }
     c->stream = st;
     c->annealed = true;
     c->last_sweeps = S->sweeps;
@@ -498,6 +574,13 @@ static int sync_ctx(gdi_ctx *c)
 {
     cudaError_t e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
+    if (c->used_grid) {
+        int32_t err = 0;
+        e = cudaMemcpy(&err, c->g_err.p, sizeof(int32_t), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(e, "error word");
+        if (err == GDI_DEVERR_TIMEOUT) return fail(GDI_ERR_TIMEOUT, "a grid barrier wait ran out");
+        if (err) return fail(GDI_ERR_CUDA, "device error word " + std::to_string(err));
+    }
     return GDI_OK;
 }
 
@@ -576,6 +659,40 @@ int gdi_get_trace(gdi_ctx *c, uint64_t *digest, int32_t *G, int64_t *cut)
     if (G && e == cudaSuccess) e = cudaMemcpy(G, c->tr_G.p, cnt * 4, cudaMemcpyDeviceToHost);
     if (cut && e == cudaSuccess) e = cudaMemcpy(cut, c->tr_cut.p, cnt * 8, cudaMemcpyDeviceToHost);
     return e == cudaSuccess ? GDI_OK : cuda_fail(e, "trace download");
+}
+
+int gdi_configure(gdi_ctx *c, int32_t path, int32_t block, int32_t grid_limit)
+{
+    if (!c) return fail(GDI_ERR_INVALID_ARG, "null argument");
+    if (path < GDI_PATH_AUTO || path > GDI_PATH_GRID) return fail(GDI_ERR_INVALID_ARG, "unknown path");
+    if (block != 0 && block != 128 && block != 256 && block != 512 && block != 1024)
+        return fail(GDI_ERR_INVALID_ARG, "block must be 0, 128, 256, 512 or 1024");
+    if (grid_limit < 0) return fail(GDI_ERR_INVALID_ARG, "grid_limit must be >= 0");
+    c->path = path;
+    if (block) c->block = block;
+    c->grid_limit = grid_limit;
+    return GDI_OK;
+}
+
+int gdi_last_launch(gdi_ctx *c, int32_t *path, int32_t *grid, int64_t *smem_bytes, int32_t *fallbacks)
+{
+    if (!c) return fail(GDI_ERR_INVALID_ARG, "null argument");
+    if (!c->annealed) return fail(GDI_ERR_NOT_ANNEALED, "no anneal yet");
+    int rc = sync_ctx(c);
+    if (rc) return rc;
+    if (path) *path = c->used_grid ? GDI_PATH_GRID : GDI_PATH_CTA;
+    if (grid) *grid = c->last_grid;
+    if (smem_bytes) *smem_bytes = (int64_t)c->last_smem;
+    if (fallbacks) {
+        *fallbacks = 0;
+        if (c->used_grid) {
+            int32_t st[16];
+            cudaError_t e = cudaMemcpy(st, c->g_status.p, sizeof st, cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess) return cuda_fail(e, "status");
+            for (int i = 0; i < 8; ++i) *fallbacks += st[i];
+        }
+    }
+    return GDI_OK;
 }
 
 int gdi_info(gdi_ctx *c, int32_t *num_classes, int32_t *max_degree, int32_t *ecap)

@@ -1,0 +1,990 @@
+// gdi_grid.cu -- grid-scale GDI anneal for graphs too large for one block (e.g. 10^6 vertices).
+//
+// Semantics are those of the CTA-resident kernel (Algorithm 3 of arXiv:1908.00210, serialised:
+// colour classes in order, windows of W ranks, inside a window the +1 group by threshold ascending
+// then the -1 group by threshold descending, each seeing the exact running G).  What changes is
+// how the chain of windows is evaluated when a class holds thousands of windows spread over every
+// SM:
+//
+//   * up to 8 replicas share one byte per vertex (bit r set = spin of replica r is -1), so one
+//     gather of a neighbour byte feeds all of them (SWAR byte-lane counters);
+//   * the map "G at window start -> G at window end" of a window is monotone; every window
+//     tabulates it for G in [c - RT, c + RT] (c = G at class start) from two small histograms of
+//     its thresholds, and each block composes the maps of its consecutive windows;
+//   * after a grid barrier one block per replica walks the P block maps (a few hundred
+//     shared-memory lookups) and publishes every block's exact input G; an entry that left the
+//     tabulated range is recomputed exactly from the spins (fallback);
+//   * after a second barrier every block replays its windows with the exact input, flips, and a
+//     third barrier makes the class's spins visible to the next class.
+//
+// Grid barriers are sense/generation barriers on global counters with a bounded spin: a block that
+// waits too long sets the error word and the kernel returns (GDI_ERR_TIMEOUT on the host).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gdi_device.cuh"
+#include "gdi_internal.h"
+
+using namespace gdi;
+
+namespace {
+
+constexpr int GB = 512;                 // threads per block
+constexpr int NWARP = GB / 32;
+constexpr int RT = 64;                  // tables cover G in [c - RT, c + RT]
+constexpr int TW = 2 * RT + 1;
+static_assert(TW == GDI_GRID_TW, "table width mismatch");
+constexpr int KC = 31;                  // flips per group a table entry can represent
+constexpr int HB = 2 * RT + 4 * KC + 1; // histogram bins for building a window table
+constexpr int HA = 2 * KC + 1;          // histogram bins for the exact apply
+constexpr int16_t TINV = INT16_MIN;
+constexpr int LONG_ROW = 48;
+constexpr long long SPIN_LIMIT = 1ll << 26;
+
+__device__ __forceinline__ uint64_t spread8(uint32_t b)
+{
+    return (((uint64_t)(b & 0x7Fu) * 0x0002040810204081ull) & 0x0101010101010101ull) |
+           ((uint64_t)(b >> 7) << 56);
+}
+
+struct GridLayout {
+    int spc, wpc, P, max_row;
+    size_t off_h, off_gam, off_s0, off_fm, off_longq, off_wtab, off_win, off_hist, off_ctab, off_row,
+        off_misc, total;
+};
+
+__host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+__host__ __device__ inline GridLayout grid_layout(int spc, int wpc, int P, int max_row)
+{
+    GridLayout L;
+    L.spc = spc;
+    L.wpc = wpc;
+    L.P = P;
+    L.max_row = max_row;
+    size_t o = 0;
+    L.off_h = o; o = align16(o + (size_t)spc * 8 * sizeof(int16_t));
+    L.off_gam = o; o = align16(o + (size_t)spc * 8 * sizeof(int32_t));
+    L.off_s0 = o; o = align16(o + (size_t)spc);
+    L.off_fm = o; o = align16(o + (size_t)((spc + 3) / 4) * sizeof(uint32_t));
+    L.off_longq = o; o = align16(o + (size_t)spc * sizeof(int32_t));
+    L.off_wtab = o; o = align16(o + (size_t)wpc * 8 * TW * sizeof(int16_t));
+    L.off_win = o; o = align16(o + (size_t)wpc * 8 * sizeof(int32_t));
+    L.off_hist = o; o = align16(o + (size_t)NWARP * 2 * HB * sizeof(int32_t));
+    L.off_ctab = o; o = align16(o + (size_t)P * TW * sizeof(int16_t));
+    L.off_row = o; o = align16(o + (size_t)(max_row + 4) * sizeof(uint32_t));
+    L.off_misc = o; o = align16(o + 64 * sizeof(int64_t));
+    L.total = o;
+    return L;
+}
+
+struct GridArgs {
+    GdiDevProblem P;
+    GdiDevRun R;
+    GdiGridScratch X;
+    int rep_base, nrep;
+    int spc, wpc;
+};
+
+// ---------------------------------------------------------------------------------------------
+// bounded grid barrier; returns false (and the caller must return) if any block timed out
+__device__ bool grid_sync(const GdiGridScratch &X)
+{
+    __syncthreads();
+    __shared__ int ok;
+    if (threadIdx.x == 0) {
+        volatile unsigned int *gen = X.bar + 1;
+        const unsigned int g0 = *gen;
+        __threadfence();
+        const unsigned int arrived = atomicAdd(X.bar, 1u);
+        int good = 1;
+        if (arrived == gridDim.x - 1) {
+            atomicExch(X.bar, 0u);
+            __threadfence();
+            atomicAdd((unsigned int *)gen, 1u);
+        } else {
+            long long spins = 0;
+            while (*gen == g0) {
+                if (++spins > SPIN_LIMIT) {
+                    atomicExch(X.err, GDI_DEVERR_TIMEOUT);
+                    good = 0;
+                    break;
+                }
+                if (*(volatile int *)X.err) { good = 0; break; }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        if (*(volatile int *)X.err) good = 0;
+        ok = good;
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+// local fields of one rank for all 8 replicas (thread-serial over the row)
+__device__ void field8_thread(const GdiDevProblem &P, int64_t base, int32_t r, const uint8_t *packed,
+                              int32_t h[8])
+{
+    const int64_t e0 = P.row_ptr[base + r], e1 = P.row_ptr[base + r + 1];
+    uint64_t aP = 0, aN = 0;
+    int32_t cP[8], cN[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) { cP[k] = 0; cN[k] = 0; }
+    int32_t nP = 0, nN = 0, cnt = 0;
+    for (int64_t e = e0; e < e1; ++e) {
+        const uint32_t c = __ldg(P.col + e);
+        const uint64_t s = spread8(__ldcg(packed + base + (c & 0x7FFFFFFFu)));
+        if (c >> 31) { aN += s; ++nN; } else { aP += s; ++nP; }
+        if (++cnt == 255) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                cP[k] += (int32_t)((aP >> (8 * k)) & 0xFF);
+                cN[k] += (int32_t)((aN >> (8 * k)) & 0xFF);
+            }
+            aP = aN = 0;
+            cnt = 0;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        cP[k] += (int32_t)((aP >> (8 * k)) & 0xFF);
+        cN[k] += (int32_t)((aN >> (8 * k)) & 0xFF);
+        h[k] = (nP - nN) - 2 * (cP[k] - cN[k]);   // sum w (1 - 2 bit) = sum w - 2 sum w bit
+    }
+}
+
+// the same for one long row, by a whole warp; the result is valid in every lane
+__device__ void field8_warp(const GdiDevProblem &P, int64_t base, int32_t r, const uint8_t *packed,
+                            int32_t h[8])
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t e0 = P.row_ptr[base + r], e1 = P.row_ptr[base + r + 1];
+    uint64_t aP = 0, aN = 0;
+    int32_t cP[8], cN[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) { cP[k] = 0; cN[k] = 0; }
+    int32_t nP = 0, nN = 0, cnt = 0;
+    for (int64_t e = e0 + lane; e < e1; e += 32) {
+        const uint32_t c = __ldg(P.col + e);
+        const uint64_t s = spread8(__ldcg(packed + base + (c & 0x7FFFFFFFu)));
+        if (c >> 31) { aN += s; ++nN; } else { aP += s; ++nP; }
+        if (++cnt == 255) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                cP[k] += (int32_t)((aP >> (8 * k)) & 0xFF);
+                cN[k] += (int32_t)((aN >> (8 * k)) & 0xFF);
+            }
+            aP = aN = 0;
+            cnt = 0;
+        }
+    }
+    nP = warp_sum(nP);
+    nN = warp_sum(nN);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const int32_t p = warp_sum(cP[k] + (int32_t)((aP >> (8 * k)) & 0xFF));
+        const int32_t q = warp_sum(cN[k] + (int32_t)((aN >> (8 * k)) & 0xFF));
+        h[k] = (nP - nN) - 2 * (p - q);
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Exact decision of one group of one window for one replica, by one warp.
+// Members are window positions i in [ws, we) whose start sign (bit r of s0[i]) is the group's;
+// gam[i * gs + r] are their thresholds.  +1 group: the k-th member in (gamma asc, position asc)
+// order flips iff g - 2k >= gamma_(k).  -1 group: (gamma desc, position asc), flips iff
+// g + 2k <= gamma_(k).  Returns the number of flips K; marks them in fm (if fm != null).
+__device__ int32_t warp_count(const int32_t *gam, int gs, int gc, const uint8_t *s0, int r, int ws,
+                              int we, bool plus, int64_t v)
+{
+    const int lane = threadIdx.x & 31;
+    int32_t c = 0;
+    for (int i = ws + lane; i < we; i += 32) {
+        const bool neg = (s0[i] >> r) & 1;
+        if (plus != !neg) continue;
+        const int64_t gm = gam[(size_t)i * gs + gc];
+        c += plus ? (gm <= v) : (gm >= v);
+    }
+    return warp_sum(c);
+}
+
+__device__ int32_t warp_group(const int32_t *gam, int gs, int gc, const uint8_t *s0, int r, int ws,
+                              int we, int32_t g, bool plus, int32_t *bins, uint32_t *fm)
+{
+    const int lane = threadIdx.x & 31;
+    // histogram of thresholds over [g - 2KC, g] (+) or [g, g + 2KC] (-); beyond: "deep" members
+    const int64_t base = plus ? (int64_t)g - 2 * KC : (int64_t)g;
+    for (int b = lane; b < HA; b += 32) bins[b] = 0;
+    __syncwarp();
+    int32_t deep = 0;
+    for (int i = ws + lane; i < we; i += 32) {
+        const bool neg = (s0[i] >> r) & 1;
+        if (plus == neg) continue;
+        const int64_t gm = gam[(size_t)i * gs + gc];
+        const int64_t b = gm - base;
+        if (plus) {
+            if (b < 0) ++deep;
+            else if (b < HA) atomicAdd(&bins[b], 1);
+        } else {
+            if (b >= HA) ++deep;
+            else if (b >= 0) atomicAdd(&bins[b], 1);
+        }
+    }
+    deep = warp_sum(deep);
+    __syncwarp();
+    // cumulative counts toward the deep side: plus: C(base + x) = deep + sum_{b <= x};
+    // minus: D(base + x) = deep + sum_{b >= x}
+    if (lane == 0) {
+        int32_t run = deep;
+        if (plus) {
+            for (int b = 0; b < HA; ++b) { run += bins[b]; bins[b] = run; }
+        } else {
+            for (int b = HA - 1; b >= 0; --b) { run += bins[b]; bins[b] = run; }
+        }
+    }
+    __syncwarp();
+    // K = #{k : count(g -/+ 2k) >= k + 1}, k in [0, KC] (one lane per k)
+    int32_t K;
+    int64_t vstar = 0;
+    int32_t t = 0;
+    bool slow;
+    {
+        const int k = lane;   // KC + 1 == 32 lanes
+        const int x = plus ? (HA - 1) - 2 * k : 2 * k;
+        const bool pred = bins[x] >= k + 1;
+        const unsigned m = __ballot_sync(0xFFFFFFFFu, pred);
+        K = __popc(m);
+        slow = (m >> 31) & 1;   // K may exceed KC
+    }
+    if (!slow) {
+        if (K == 0) return 0;
+        if (K <= deep) {
+            // all K flips are deep members (K == deep here: K >= min(deep, KC + 1))
+            vstar = plus ? base : base + HA - 1;   // flips: exactly the deep members
+            t = 0;
+        } else {
+            // v* = the K-th value in group order; t = ties at v* that flip
+            int first = -1;
+            for (int x0 = 0; x0 < HA; x0 += 32) {
+                const int x = x0 + lane;
+                bool pred = false;
+                if (x < HA) pred = plus ? (bins[x] >= K) : (bins[HA - 1 - x] >= K);
+                const unsigned m = __ballot_sync(0xFFFFFFFFu, pred);
+                if (m) { first = x0 + __ffs(m) - 1; break; }
+            }
+            if (plus) {
+                vstar = base + first;
+                const int32_t before = first > 0 ? bins[first - 1] : deep;
+                t = K - before;
+            } else {
+                const int xb = HA - 1 - first;
+                vstar = base + xb;
+                const int32_t before = xb < HA - 1 ? bins[xb + 1] : deep;
+                t = K - before;
+            }
+        }
+    } else {
+        // exact counting path: K = max{k + 1 : count(g -/+ 2k) >= k + 1}
+        const int32_t n0 = warp_count(gam, gs, gc, s0, r, ws, we, plus, g);
+        int32_t lo = 0, hi = n0;   // K in [0, n0]
+        while (lo < hi) {
+            const int32_t mid = (lo + hi + 1) >> 1;   // test k = mid - 1
+            const int64_t v = plus ? (int64_t)g - 2 * (int64_t)(mid - 1) : (int64_t)g + 2 * (int64_t)(mid - 1);
+            if (warp_count(gam, gs, gc, s0, r, ws, we, plus, v) >= mid) lo = mid; else hi = mid - 1;
+        }
+        K = lo;
+        if (K == 0) return 0;
+        // v*: plus: smallest v with C(v) >= K; minus: largest v with D(v) >= K
+        int64_t a = -((int64_t)1 << 31), b = (int64_t)1 << 31;
+        if (plus) {
+            b = (int64_t)g - 2 * (int64_t)(K - 1);
+            while (a < b) {
+                const int64_t mid = a + ((b - a) >> 1);
+                if (warp_count(gam, gs, gc, s0, r, ws, we, true, mid) >= K) b = mid; else a = mid + 1;
+            }
+            vstar = a;
+            t = K - warp_count(gam, gs, gc, s0, r, ws, we, true, vstar - 1);
+        } else {
+            a = (int64_t)g + 2 * (int64_t)(K - 1);
+            while (a < b) {
+                const int64_t mid = a + ((b - a + 1) >> 1);
+                if (warp_count(gam, gs, gc, s0, r, ws, we, false, mid) >= K) a = mid; else b = mid - 1;
+            }
+            vstar = a;
+            t = K - warp_count(gam, gs, gc, s0, r, ws, we, false, vstar + 1);
+        }
+    }
+    if (fm) {
+        int32_t run = 0;
+        for (int i0 = ws; i0 < we; i0 += 32) {
+            const int i = i0 + lane;
+            bool mem = false, strict = false, tie = false;
+            if (i < we) {
+                const bool neg = (s0[i] >> r) & 1;
+                mem = (plus != neg);
+                if (mem) {
+                    const int64_t gm = gam[(size_t)i * gs + gc];
+                    strict = plus ? (gm < vstar) : (gm > vstar);
+                    tie = (gm == vstar);
+                }
+            }
+            const unsigned tm = __ballot_sync(0xFFFFFFFFu, tie);
+            const int32_t idx = run + __popc(tm & ((1u << lane) - 1u));
+            run += __popc(tm);
+            if (strict || (tie && idx < t)) atomicOr(&fm[i >> 2], 1u << (8 * (i & 3) + r));
+        }
+    }
+    return K;
+}
+
+// ---------------------------------------------------------------------------------------------
+struct GSmem {
+    int16_t *h;        // [spc][8]
+    int32_t *gam;      // [spc][8]
+    uint8_t *s0;       // [spc]
+    uint32_t *fm;      // [spc/4]
+    int32_t *longq;    // [spc]
+    int16_t *wtab;     // [wpc][8][TW]
+    int32_t *win;      // [wpc][8]
+    int32_t *hist;     // [NWARP][2][HB]
+    int16_t *ctab;     // [P][TW]
+    uint32_t *row;     // [max_row]
+    int64_t *misc;     // scratch
+};
+
+__device__ inline void class_partition(int32_t lo, int32_t hi, int W, int p, int P, int32_t &a0,
+                                       int32_t &a1, int &nwin)
+{
+    const int32_t nw = (hi - lo + W - 1) / W;
+    const int32_t k0 = (int32_t)(((int64_t)p * nw) / P);
+    const int32_t k1 = (int32_t)(((int64_t)(p + 1) * nw) / P);
+    a0 = lo + k0 * W;
+    a1 = min(lo + k1 * W, hi);
+    if (a1 < a0) a1 = a0;
+    nwin = k1 - k0;
+}
+
+// Thresholds of the spin range [a0, a1).  all_reps: every replica, stored [i*8 + r] (fields in
+// hbuf [i*8 + r], rows longer than LONG_ROW summed by a warp).  Otherwise only replica `one`,
+// stored [i] with fields [i] (thread-serial rows; used by the rare exact fallback).
+__device__ void range_thresholds(const GridArgs &A, const GSmem &S, int32_t a0, int32_t a1, int sw,
+                                 bool all_reps, int one, int32_t *gam_out, uint8_t *s0_out,
+                                 int16_t *hbuf, int32_t rlen, float Tsw)
+{
+    const GdiDevProblem &P = A.P;
+    const int64_t base = P.node_off[0];
+    const uint8_t *packed = A.X.packed;
+    const int32_t ns = a1 - a0;
+    const int hs = all_reps ? 8 : 1;
+    __shared__ int nlong;
+    if (threadIdx.x == 0) nlong = 0;
+    __syncthreads();
+    for (int32_t i = threadIdx.x; i < ns; i += GB) {
+        const int32_t rk = a0 + i;
+        s0_out[i] = __ldcg(packed + base + rk);
+        const int64_t deg = P.row_ptr[base + rk + 1] - P.row_ptr[base + rk];
+        if (all_reps && deg > LONG_ROW) {
+            S.longq[atomicAdd(&nlong, 1)] = i;
+        } else {
+            int32_t h[8];
+            field8_thread(P, base, rk, packed, h);
+            if (all_reps) {
+#pragma unroll
+                for (int k = 0; k < 8; ++k) hbuf[(size_t)i * 8 + k] = (int16_t)h[k];
+            } else {
+#pragma unroll
+                for (int k = 0; k < 8; ++k)
+                    if (k == one) hbuf[i] = (int16_t)h[k];
+            }
+        }
+    }
+    __syncthreads();
+    if (all_reps) {
+        const int nl = nlong;
+        for (int t = threadIdx.x >> 5; t < nl; t += NWARP) {
+            const int32_t i = S.longq[t];
+            int32_t h[8];
+            field8_warp(P, base, a0 + i, packed, h);
+            if ((threadIdx.x & 31) == 0)
+#pragma unroll
+                for (int k = 0; k < 8; ++k) hbuf[(size_t)i * 8 + k] = (int16_t)h[k];
+        }
+        __syncthreads();
+    }
+    if (ns > 0) {
+        const int32_t q0 = a0 >> 2, q1 = (a1 - 1) >> 2;
+        const int nr = all_reps ? A.nrep : 1;
+        const int64_t tasks = (int64_t)(q1 - q0 + 1) * nr;
+        for (int64_t t = threadIdx.x; t < tasks; t += GB) {
+            const int32_t qd = q0 + (int32_t)(t / nr);
+            const int r = all_reps ? (int)(t % nr) : one;
+            const uint4 u4 = philox4x32_10(make_uint4((uint32_t)qd, (uint32_t)sw, 0u,
+                                                      (uint32_t)(A.rep_base + r)),
+                                           A.R.key0, A.R.key1);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int32_t rk = 4 * qd + j;
+                if (rk < a0 || rk >= a1) continue;
+                const int32_t i = rk - a0;
+                const int sg = ((s0_out[i] >> r) & 1) ? -1 : 1;
+                const int32_t h = hbuf[(size_t)i * hs + (all_reps ? r : 0)];
+                const int32_t es = estar_of(S.row, rlen, A.R.mode, word_of(u4, j), Tsw);
+                gam_out[(size_t)i * hs + (all_reps ? r : 0)] = gamma_of(sg, h, es, P.A, P.B);
+            }
+        }
+    }
+    __syncthreads();
+}
+
+// table of one window (positions [ws, we)) for replica r over G in [c - RT, c + RT], by one warp
+__device__ void window_table(const GSmem &S, int ws, int we, int r, int32_t c, bool plus_first,
+                             int32_t *hp, int32_t *hm, int16_t *tab)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t base = (int64_t)c - RT - 2 * KC;
+    for (int b = lane; b < HB; b += 32) { hp[b] = 0; hm[b] = 0; }
+    __syncwarp();
+    int32_t under = 0, over = 0;
+    for (int i = ws + lane; i < we; i += 32) {
+        const bool neg = (S.s0[i] >> r) & 1;
+        const int64_t b = (int64_t)S.gam[(size_t)i * 8 + r] - base;
+        if (!neg) {
+            if (b < 0) ++under;
+            else if (b < HB) atomicAdd(&hp[b], 1);
+        } else {
+            if (b >= HB) ++over;
+            else if (b >= 0) atomicAdd(&hm[b], 1);
+        }
+    }
+    under = warp_sum(under);
+    over = warp_sum(over);
+    __syncwarp();
+    if (lane == 0) {
+        int32_t run = under;
+        for (int b = 0; b < HB; ++b) { run += hp[b]; hp[b] = run; }          // C(base + b)
+        run = over;
+        for (int b = HB - 1; b >= 0; --b) { run += hm[b]; hm[b] = run; }     // D(base + b)
+    }
+    __syncwarp();
+    for (int e = lane; e < TW; e += 32) {
+        int64_t g = (int64_t)c - RT + e;
+        bool valid = true;
+        for (int ph = 0; ph < 2 && valid; ++ph) {
+            const bool plus = plus_first ? (ph == 0) : (ph == 1);
+            int32_t K = 0;
+            bool capped = true;
+            for (int k = 0; k <= KC; ++k) {
+                const int64_t v = plus ? g - 2 * k : g + 2 * k;
+                const int64_t x = v - base;
+                const int32_t cnt = plus ? hp[x] : hm[x];
+                if (cnt >= k + 1) K = k + 1; else { capped = false; break; }
+            }
+            if (capped) valid = false;
+            g = plus ? g - 2 * K : g + 2 * K;
+        }
+        tab[e] = valid ? (int16_t)(g - ((int64_t)c - RT)) : TINV;
+    }
+    __syncwarp();
+}
+
+// exact output G of a window (both groups), by one warp
+__device__ int32_t window_exact(const int32_t *gam, int gs, int gc, const uint8_t *s0, int r, int ws,
+                                int we, int32_t g, bool plus_first, int32_t *bins)
+{
+    const int32_t K1 = warp_group(gam, gs, gc, s0, r, ws, we, g, plus_first, bins, nullptr);
+    g = plus_first ? g - 2 * K1 : g + 2 * K1;
+    const int32_t K2 = warp_group(gam, gs, gc, s0, r, ws, we, g, !plus_first, bins, nullptr);
+    return plus_first ? g + 2 * K2 : g - 2 * K2;
+}
+
+__global__ void __launch_bounds__(GB, 1) gdi_grid_anneal_kernel(GridArgs A)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int chain_pp;
+    __shared__ int32_t chain_g;
+    const GdiDevProblem &P = A.P;
+    const GdiDevRun &R = A.R;
+    const GdiGridScratch &X = A.X;
+    const int Pb = gridDim.x, p = blockIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const GridLayout L = grid_layout(A.spc, A.wpc, Pb, R.max_row);
+    GSmem S;
+    S.h = reinterpret_cast<int16_t *>(smem_raw + L.off_h);
+    S.gam = reinterpret_cast<int32_t *>(smem_raw + L.off_gam);
+    S.s0 = reinterpret_cast<uint8_t *>(smem_raw + L.off_s0);
+    S.fm = reinterpret_cast<uint32_t *>(smem_raw + L.off_fm);
+    S.longq = reinterpret_cast<int32_t *>(smem_raw + L.off_longq);
+    S.wtab = reinterpret_cast<int16_t *>(smem_raw + L.off_wtab);
+    S.win = reinterpret_cast<int32_t *>(smem_raw + L.off_win);
+    S.hist = reinterpret_cast<int32_t *>(smem_raw + L.off_hist);
+    S.ctab = reinterpret_cast<int16_t *>(smem_raw + L.off_ctab);
+    S.row = reinterpret_cast<uint32_t *>(smem_raw + L.off_row);
+    S.misc = reinterpret_cast<int64_t *>(smem_raw + L.off_misc);
+    int32_t *Gc = reinterpret_cast<int32_t *>(S.misc);   // [8] class-start G of each replica
+    const int64_t base = P.node_off[0];
+    const int32_t n = (int32_t)(P.node_off[1] - base);
+    const int32_t *cls = P.class_ptr + P.class_off[0];
+    const int32_t ncls = P.class_off[1] - P.class_off[0] - 1;
+    const int W = P.W;
+    const int nrep = A.nrep;
+
+    // G of every replica: n - 2 #(-1)   (X.Gcls zeroed by the host)
+    {
+        int32_t cntm[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        const int32_t r0 = (int32_t)(((int64_t)p * n) / Pb), r1 = (int32_t)(((int64_t)(p + 1) * n) / Pb);
+        for (int32_t i = r0 + threadIdx.x; i < r1; i += GB) {
+            const uint8_t b = __ldcg(X.packed + base + i);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) cntm[k] += (b >> k) & 1;
+        }
+        for (int k = 0; k < nrep; ++k) {
+            const int32_t m = warp_sum(cntm[k]);
+            if (lane == 0 && m) atomicAdd(&X.Gcls[k], -2 * m);
+        }
+        if (p == 0 && threadIdx.x < nrep) atomicAdd(&X.Gcls[threadIdx.x], n);
+    }
+    if (!grid_sync(X)) return;
+
+    for (int sw = R.s_begin; sw < R.s_end; ++sw) {
+        const int32_t roff = R.tab_off[sw];
+        const int32_t rlen = R.tab_off[sw + 1] - roff;
+        for (int k = threadIdx.x; k < rlen; k += GB) S.row[k] = R.tab[roff + k];
+        const float Tsw = R.temp ? R.temp[sw] : 0.f;
+        const bool plus_first = (sw & 1) == 0;
+        __syncthreads();
+        for (int c = 0; c < ncls; ++c) {
+            const int32_t lo = cls[c], hi = cls[c + 1];
+            int32_t a0, a1;
+            int nwin;
+            class_partition(lo, hi, W, p, Pb, a0, a1, nwin);
+            if (threadIdx.x < nrep) Gc[threadIdx.x] = *(volatile int32_t *)&X.Gcls[threadIdx.x];
+            // ---- phase A: thresholds of my windows, window tables, block table
+            range_thresholds(A, S, a0, a1, sw, true, 0, S.gam, S.s0, S.h, rlen, Tsw);
+            for (int task = warp; task < nwin * nrep; task += NWARP) {
+                const int kk = task / nrep, r = task % nrep;
+                const int ws = kk * W, we = min(ws + W, a1 - a0);
+                window_table(S, ws, we, r, Gc[r], plus_first, S.hist + (size_t)warp * 2 * HB,
+                             S.hist + (size_t)warp * 2 * HB + HB, S.wtab + ((size_t)kk * 8 + r) * TW);
+            }
+            __syncthreads();
+            if (warp < nrep) {
+                const int r = warp;
+                for (int e = lane; e < TW; e += 32) {
+                    int32_t idx = e;
+                    for (int kk = 0; kk < nwin; ++kk) {
+                        if (idx < 0 || idx >= TW) { idx = TINV; break; }
+                        const int16_t v = S.wtab[((size_t)kk * 8 + r) * TW + idx];
+                        if (v == TINV) { idx = TINV; break; }
+                        idx = v;
+                    }
+                    X.tables[((size_t)p * 8 + r) * TW + e] = (int16_t)idx;
+                }
+            }
+            if (!grid_sync(X)) return;
+            // ---- phase C: one block per replica chains the block tables
+            if (p < nrep) {
+                const int r = p;
+                for (int64_t t = threadIdx.x; t < (int64_t)Pb * TW; t += GB) {
+                    const int pp = (int)(t / TW), e = (int)(t % TW);
+                    S.ctab[(size_t)pp * TW + e] = __ldcg(X.tables + ((size_t)pp * 8 + r) * TW + e);
+                }
+                const int32_t c0 = Gc[r];
+                if (threadIdx.x == 0) { chain_pp = 0; chain_g = c0; }
+                __syncthreads();
+                while (true) {
+                    if (threadIdx.x == 0) {
+                        int pp = chain_pp;
+                        int32_t g = chain_g;
+                        while (pp < Pb) {
+                            const int64_t idx = (int64_t)g - ((int64_t)c0 - RT);
+                            if (idx < 0 || idx >= TW) break;
+                            const int16_t v = S.ctab[(size_t)pp * TW + idx];
+                            if (v == TINV) break;
+                            X.gin[(size_t)pp * 8 + r] = g;
+                            g = (int32_t)((int64_t)c0 - RT + v);
+                            ++pp;
+                        }
+                        chain_pp = pp;
+                        chain_g = g;
+                    }
+                    __syncthreads();
+                    const int pp = chain_pp;
+                    const int32_t g = chain_g;
+                    __syncthreads();
+                    if (pp >= Pb) break;
+                    // exact fallback for block pp: its thresholds for replica r, recomputed into the
+                    // histogram area (free during this phase)
+                    if (threadIdx.x == 0) X.gin[(size_t)pp * 8 + r] = g;
+                    int32_t b0, b1;
+                    int nw2;
+                    class_partition(lo, hi, W, pp, Pb, b0, b1, nw2);
+                    const int32_t nb = b1 - b0;
+                    int32_t *fg = S.hist;
+                    int16_t *fh = reinterpret_cast<int16_t *>(fg + nb);
+                    uint8_t *fs = reinterpret_cast<uint8_t *>(fh + ((nb + 7) & ~7));
+                    int32_t *fbins = reinterpret_cast<int32_t *>(fs + ((nb + 15) & ~15));
+                    range_thresholds(A, S, b0, b1, sw, false, r, fg, fs, fh, rlen, Tsw);
+                    if (warp == 0) {
+                        int32_t gg = g;
+                        for (int kk = 0; kk < nw2; ++kk) {
+                            const int ws = kk * W, we = min(ws + W, nb);
+                            gg = window_exact(fg, 1, 0, fs, r, ws, we, gg, plus_first, fbins);
+                        }
+                        if (lane == 0) {
+                            chain_pp = pp + 1;
+                            chain_g = gg;
+                            atomicAdd(X.status + r, 1);
+                        }
+                    }
+                    __syncthreads();
+                }
+                if (threadIdx.x == 0) X.Gcls[r] = chain_g;
+            }
+            if (!grid_sync(X)) return;
+            // ---- phase D: inputs of my windows, then the exact flips of every (window, replica)
+            for (int i = threadIdx.x; i < (a1 - a0 + 3) / 4; i += GB) S.fm[i] = 0;
+            if (warp < nrep) {
+                const int r = warp;
+                int32_t g = __ldcg(X.gin + (size_t)p * 8 + r);
+                const int32_t cbase = Gc[r] - RT;
+                int32_t *bins = S.hist + (size_t)warp * 2 * HB;
+                for (int kk = 0; kk < nwin; ++kk) {
+                    if (lane == 0) S.win[kk * 8 + r] = g;
+                    const int64_t idx = (int64_t)g - cbase;
+                    int16_t v = TINV;
+                    if (idx >= 0 && idx < TW) v = S.wtab[((size_t)kk * 8 + r) * TW + idx];
+                    if (v != TINV) {
+                        g = cbase + v;
+                    } else {
+                        const int ws = kk * W, we = min(ws + W, a1 - a0);
+                        g = window_exact(S.gam, 8, r, S.s0, r, ws, we, g, plus_first, bins);
+                    }
+                }
+            }
+            __syncthreads();
+            for (int task = warp; task < nwin * nrep; task += NWARP) {
+                const int kk = task / nrep, r = task % nrep;
+                const int ws = kk * W, we = min(ws + W, a1 - a0);
+                int32_t *bins = S.hist + (size_t)warp * 2 * HB;
+                int32_t g = S.win[kk * 8 + r];
+                const int32_t K1 = warp_group(S.gam, 8, r, S.s0, r, ws, we, g, plus_first, bins, S.fm);
+                g = plus_first ? g - 2 * K1 : g + 2 * K1;
+                warp_group(S.gam, 8, r, S.s0, r, ws, we, g, !plus_first, bins, S.fm);
+            }
+            __syncthreads();
+            for (int32_t i = threadIdx.x; i < a1 - a0; i += GB) {
+                const uint8_t f = (uint8_t)(S.fm[i >> 2] >> (8 * (i & 3)));
+                if (f) X.packed[base + a0 + i] = S.s0[i] ^ f;
+            }
+            if (!grid_sync(X)) return;
+        }
+        if (R.flags & GDI_DEV_TRACE) {
+            // digest and cut of every replica after this sweep (grid-wide atomics)
+            const int32_t r0 = (int32_t)(((int64_t)p * n) / Pb), r1 = (int32_t)(((int64_t)(p + 1) * n) / Pb);
+            uint64_t dg[8];
+            int64_t ct[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) { dg[k] = 0; ct[k] = 0; }
+            for (int32_t i = r0 + threadIdx.x; i < r1; i += GB) {
+                const uint8_t b = __ldcg(X.packed + base + i);
+                for (int k = 0; k < nrep; ++k)
+                    if (!((b >> k) & 1))
+                        dg[k] += splitmix64_fin((uint64_t)(uint32_t)i | ((uint64_t)(sw & 0xFFFF) << 32) |
+                                                ((uint64_t)((A.rep_base + k) & 0xFFFF) << 48));
+                const int64_t e0 = P.row_ptr[base + i], e1 = P.row_ptr[base + i + 1];
+                for (int64_t e = e0; e < e1; ++e) {
+                    const uint32_t cc = __ldg(P.col + e);
+                    const uint32_t j = cc & 0x7FFFFFFFu;
+                    if ((int32_t)j <= i) continue;
+                    const uint8_t d = b ^ __ldcg(X.packed + base + j);
+                    if (!d) continue;
+                    for (int k = 0; k < nrep; ++k)
+                        if ((d >> k) & 1) ct[k] += (cc >> 31) ? -1 : 1;
+                }
+            }
+            for (int k = 0; k < nrep; ++k) {
+                const uint64_t a = warp_sum(dg[k]);
+                const int64_t b = warp_sum(ct[k]);
+                const int64_t o = (int64_t)(A.rep_base + k) * R.sweeps + sw;
+                if (lane == 0) {
+                    if (a) atomicAdd((unsigned long long *)(R.tr_digest + o), (unsigned long long)a);
+                    if (b) atomicAdd((unsigned long long *)(R.tr_cut + o), (unsigned long long)b);
+                }
+            }
+            if (p == 0 && threadIdx.x < nrep)
+                R.tr_G[(int64_t)(A.rep_base + threadIdx.x) * R.sweeps + sw] =
+                    *(volatile int32_t *)&X.Gcls[threadIdx.x];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// replica group <-> int8 spins in rank space
+__global__ void pack_kernel(int8_t *spins, int64_t N, int rep_base, int nrep, uint8_t *packed)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t b = 0;
+        for (int r = 0; r < nrep; ++r) b |= (spins[(int64_t)(rep_base + r) * N + i] < 0 ? 1u : 0u) << r;
+        packed[i] = (uint8_t)b;
+    }
+}
+
+__global__ void unpack_kernel(int8_t *spins, int64_t N, int rep_base, int nrep, const uint8_t *packed)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint8_t b = packed[i];
+        for (int r = 0; r < nrep; ++r) spins[(int64_t)(rep_base + r) * N + i] = ((b >> r) & 1) ? -1 : 1;
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// cut and exact-balance repair of a single large instance, replica by replica (int8 spins)
+__device__ __forceinline__ int32_t field_i8(const GdiDevProblem &P, const int8_t *s, int64_t r)
+{
+    int32_t h = 0;
+    for (int64_t e = P.row_ptr[r]; e < P.row_ptr[r + 1]; ++e) {
+        const uint32_t c = __ldg(P.col + e);
+        const int32_t v = s[c & 0x7FFFFFFFu];
+        h += (c >> 31) ? -v : v;
+    }
+    return h;
+}
+
+__global__ void cut_kernel(GdiDevProblem P, const int8_t *spins, int nrep, int64_t *cut)
+{
+    const int64_t N = P.N;
+    for (int r = 0; r < nrep; ++r) {
+        const int8_t *s = spins + (int64_t)r * N;
+        int64_t c = 0;
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+            for (int64_t e = P.row_ptr[i]; e < P.row_ptr[i + 1]; ++e) {
+                const uint32_t cc = __ldg(P.col + e);
+                const int64_t j = cc & 0x7FFFFFFFu;
+                if (j > i && s[j] != s[i]) c += (cc >> 31) ? -1 : 1;
+            }
+        }
+        c = warp_sum(c);
+        if ((threadIdx.x & 31) == 0 && c) atomicAdd((unsigned long long *)(cut + r), (unsigned long long)c);
+    }
+}
+
+// per replica: k = (|G| - n mod 2) / 2 majority spins with the smallest (s h, rank) keys flip.
+// rp[r*4 + 0..3] = k, majority sign, kappa (smallest key with count(key <= kappa) >= k), t (ties)
+__global__ void repair_hist_kernel(GdiDevProblem P, const int8_t *spins, int nrep, const int32_t *G,
+                                   int32_t *hist, int32_t D)
+{
+    const int64_t N = P.N;
+    for (int r = 0; r < nrep; ++r) {
+        const int32_t g = G[r];
+        const int32_t tgt = (int32_t)(N & 1);
+        if ((g < 0 ? -g : g) <= tgt) continue;
+        const int8_t maj = g > 0 ? 1 : -1;
+        const int8_t *s = spins + (int64_t)r * N;
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+            if (s[i] != maj) continue;
+            const int32_t key = maj * field_i8(P, s, i);
+            atomicAdd(&hist[(int64_t)r * (2 * D + 1) + key + D], 1);
+        }
+    }
+}
+
+__global__ void repair_select_kernel(const int32_t *G, int64_t N, const int32_t *hist, int32_t D, int32_t *rp)
+{
+    const int r = blockIdx.x;
+    if (threadIdx.x != 0) return;
+    const int32_t g = G[r];
+    const int32_t tgt = (int32_t)(N & 1);
+    const int32_t ag = g < 0 ? -g : g;
+    int32_t k = ag > tgt ? (ag - tgt) / 2 : 0;
+    rp[r * 4 + 0] = k;
+    rp[r * 4 + 1] = g > 0 ? 1 : -1;
+    rp[r * 4 + 2] = 0;
+    rp[r * 4 + 3] = 0;
+    if (k == 0) return;
+    int32_t run = 0;
+    for (int32_t b = 0; b < 2 * D + 1; ++b) {
+        const int32_t hb = hist[(int64_t)r * (2 * D + 1) + b];
+        if (run + hb >= k) {
+            rp[r * 4 + 2] = b - D;
+            rp[r * 4 + 3] = k - run;
+            return;
+        }
+        run += hb;
+    }
+}
+
+// ties (key == kappa) per block in rank order, then the flip flags
+__global__ void repair_ties_kernel(GdiDevProblem P, const int8_t *spins, int nrep, const int32_t *rp,
+                                   int32_t *ties, int64_t chunk)
+{
+    const int64_t N = P.N;
+    const int64_t i0 = (int64_t)blockIdx.x * chunk, i1 = min(N, i0 + chunk);
+    for (int r = 0; r < nrep; ++r) {
+        if (rp[r * 4] == 0) { if (threadIdx.x == 0) ties[(int64_t)r * gridDim.x + blockIdx.x] = 0; continue; }
+        const int8_t maj = (int8_t)rp[r * 4 + 1];
+        const int32_t kappa = rp[r * 4 + 2];
+        const int8_t *s = spins + (int64_t)r * N;
+        int32_t c = 0;
+        for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x)
+            if (s[i] == maj && maj * field_i8(P, s, i) == kappa) ++c;
+        c = warp_sum(c);
+        __shared__ int32_t acc;
+        if (threadIdx.x == 0) acc = 0;
+        __syncthreads();
+        if ((threadIdx.x & 31) == 0) atomicAdd(&acc, c);
+        __syncthreads();
+        if (threadIdx.x == 0) ties[(int64_t)r * gridDim.x + blockIdx.x] = acc;
+        __syncthreads();
+    }
+}
+
+__global__ void repair_mark_kernel(GdiDevProblem P, const int8_t *spins, int nrep, const int32_t *rp,
+                                   const int32_t *ties, int64_t chunk, uint8_t *flags)
+{
+    // blockDim.x == 256; ranks of the chunk are visited in rounds of 256 in rank order
+    const int64_t N = P.N;
+    const int64_t i0 = (int64_t)blockIdx.x * chunk, i1 = min(N, i0 + chunk);
+    __shared__ int32_t before;
+    __shared__ int32_t wsum[8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int r = 0; r < nrep; ++r) {
+        if (rp[r * 4] == 0) continue;
+        const int8_t maj = (int8_t)rp[r * 4 + 1];
+        const int32_t kappa = rp[r * 4 + 2], t = rp[r * 4 + 3];
+        const int8_t *s = spins + (int64_t)r * N;
+        if (threadIdx.x == 0) {
+            int32_t b = 0;
+            for (int q = 0; q < (int)blockIdx.x; ++q) b += ties[(int64_t)r * gridDim.x + q];
+            before = b;
+        }
+        __syncthreads();
+        int32_t run = before;
+        for (int64_t j0 = i0; j0 < i1; j0 += 256) {
+            const int64_t i = j0 + threadIdx.x;
+            bool strict = false, tie = false;
+            if (i < i1 && s[i] == maj) {
+                const int32_t key = maj * field_i8(P, s, i);
+                strict = key < kappa;
+                tie = key == kappa;
+            }
+            const unsigned m = __ballot_sync(0xFFFFFFFFu, tie);
+            if (lane == 0) wsum[warp] = __popc(m);
+            __syncthreads();
+            int32_t off = run;
+            for (int w = 0; w < warp; ++w) off += wsum[w];
+            const int32_t idx = off + __popc(m & ((1u << lane) - 1u));
+            int32_t tot = 0;
+            for (int w = 0; w < 8; ++w) tot += wsum[w];
+            if (strict || (tie && idx < t)) flags[i] |= (uint8_t)(1u << r);
+            run += tot;
+            __syncthreads();
+        }
+    }
+}
+
+__global__ void repair_apply_kernel(int8_t *spins, int64_t N, int nrep, const uint8_t *flags, const int32_t *rp,
+                                    int32_t *G)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint8_t f = flags[i];
+        if (!f) continue;
+        for (int r = 0; r < nrep; ++r)
+            if ((f >> r) & 1) spins[(int64_t)r * N + i] = (int8_t)(-spins[(int64_t)r * N + i]);
+    }
+    if (blockIdx.x == 0 && threadIdx.x < nrep) {
+        const int r = threadIdx.x;
+        G[r] = G[r] - 2 * rp[r * 4 + 1] * rp[r * 4 + 0];
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------------
+int gdi_grid_fallback_fits(int spc)
+{
+    // the exact chain fallback keeps thresholds, fields, start signs and bins of one block's
+    // windows (one replica) in the histogram area
+    return (size_t)spc * 7 + 64 + HA * sizeof(int32_t) <= (size_t)NWARP * 2 * HB * sizeof(int32_t);
+}
+
+int gdi_grid_plan(const GdiDevProblem &P, int max_row, int sms, int *spc, int *wpc, size_t *smem)
+{
+    if (P.num_instances != 1 || P.W < 1) return -1;
+    // windows per block: the largest class decides
+    const int wp = (int)((P.max_class + P.W - 1) / P.W);
+    const int w = (wp + sms - 1) / sms;
+    *wpc = w < 1 ? 1 : w;
+    *spc = *wpc * P.W;
+    *smem = grid_layout(*spc, *wpc, sms, max_row).total;
+    return 0;
+}
+
+int gdi_launch_grid_anneal(const GdiDevProblem &P, const GdiDevRun &R, const GdiGridScratch &X,
+                           int8_t *spins, int sms, int spc, int wpc, size_t smem, void *stream)
+{
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaFuncSetAttribute(gdi_grid_anneal_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return (int)e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gdi_grid_anneal_kernel, GB, smem);
+    if (e != cudaSuccess) return (int)e;
+    if (per_sm < 1) return (int)cudaErrorCooperativeLaunchTooLarge;
+    const int pg = (int)((P.N + 255) / 256) < 4096 ? (int)((P.N + 255) / 256) : 4096;
+    for (int g0 = 0; g0 < P.replicas; g0 += 8) {
+        const int nrep = P.replicas - g0 < 8 ? P.replicas - g0 : 8;
+        pack_kernel<<<pg, 256, 0, st>>>(spins, P.N, g0, nrep, X.packed);
+        cudaMemsetAsync(X.Gcls, 0, 8 * sizeof(int32_t), st);
+        cudaMemsetAsync(X.bar, 0, 2 * sizeof(unsigned int), st);
+        GridArgs A;
+        A.P = P;
+        A.R = R;
+        A.X = X;
+        A.rep_base = g0;
+        A.nrep = nrep;
+        A.spc = spc;
+        A.wpc = wpc;
+        void *args[] = {&A};
+        e = cudaLaunchCooperativeKernel((const void *)gdi_grid_anneal_kernel, dim3(sms), dim3(GB), args, smem, st);
+        if (e != cudaSuccess) return (int)e;
+        unpack_kernel<<<pg, 256, 0, st>>>(spins, P.N, g0, nrep, X.packed);
+        e = cudaMemcpyAsync(R.raw_G + g0, X.Gcls, nrep * sizeof(int32_t), cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return (int)e;
+    }
+    return (int)cudaGetLastError();
+}
+
+// raw cut, repair, final cut, final G of a single instance (all replicas)
+int gdi_launch_grid_finish(const GdiDevProblem &P, const GdiDevRun &R, const GdiGridScratch &X,
+                           int8_t *spins, int do_repair, void *stream)
+{
+    cudaStream_t st = (cudaStream_t)stream;
+    const int nb = 152 * 4;
+    const int64_t N = P.N;
+    const int D = P.max_degree;
+    cudaError_t e = cudaMemsetAsync(R.raw_cut, 0, P.replicas * sizeof(int64_t), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(R.final_cut, 0, P.replicas * sizeof(int64_t), st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(R.final_G, R.raw_G, P.replicas * sizeof(int32_t), cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return (int)e;
+    cut_kernel<<<nb, 256, 0, st>>>(P, spins, P.replicas, R.raw_cut);
+    if (do_repair) {
+        for (int g0 = 0; g0 < P.replicas; g0 += 8) {
+            const int nrep = P.replicas - g0 < 8 ? P.replicas - g0 : 8;
+            int8_t *sp = spins + (int64_t)g0 * N;
+            GdiDevProblem Q = P;
+            cudaMemsetAsync(X.rhist, 0, (size_t)nrep * (2 * D + 1) * sizeof(int32_t), st);
+            cudaMemsetAsync(X.rflags, 0, (size_t)N, st);
+            repair_hist_kernel<<<nb, 256, 0, st>>>(Q, sp, nrep, R.final_G + g0, X.rhist, D);
+            repair_select_kernel<<<nrep, 32, 0, st>>>(R.final_G + g0, N, X.rhist, D, X.rparams);
+            const int64_t chunk = (N + nb - 1) / nb;
+            repair_ties_kernel<<<nb, 256, 0, st>>>(Q, sp, nrep, X.rparams, X.rties, chunk);
+            repair_mark_kernel<<<nb, 256, 0, st>>>(Q, sp, nrep, X.rparams, X.rties, chunk, X.rflags);
+            repair_apply_kernel<<<nb, 256, 0, st>>>(sp, N, nrep, X.rflags, X.rparams, R.final_G + g0);
+        }
+    }
+    cut_kernel<<<nb, 256, 0, st>>>(P, spins, P.replicas, R.final_cut);
+    return (int)cudaGetLastError();
+}
+
+size_t gdi_grid_smem(int spc, int wpc, int P, int max_row) { return grid_layout(spc, wpc, P, max_row).total; }

@@ -22,6 +22,22 @@ struct GdiDevProblem {
     int32_t max_n;                   // largest instance
     int32_t max_window;              // largest window (W or class size) over instances
     int32_t max_degree;
+    int32_t max_class;               // largest colour class
+};
+
+// Global scratch of the grid-scale path (single large instance).
+struct GdiGridScratch {
+    uint8_t *packed;                 // [N] spins of one replica group: bit r set = replica r is -1
+    int16_t *tables;                 // [P][8][TW] composed window tables of every block
+    int32_t *gin;                    // [P][8] exact G entering every block's windows
+    int32_t *Gcls;                   // [8] G at class start / after the class
+    unsigned int *bar;               // [2] grid barrier: arrival count, generation
+    int32_t *err;                    // [1] device error word
+    int32_t *status;                 // [16] diagnostics: exact fallbacks per replica
+    int32_t *rhist;                  // [8][2*max_degree+1] repair key histogram
+    uint8_t *rflags;                 // [N] repair flips (bit per replica)
+    int32_t *rties;                  // [8][blocks] repair ties per block
+    int32_t *rparams;                // [8][4] repair k, majority, kappa, ties to take
 };
 
 // One annealing call.
@@ -29,6 +45,7 @@ struct GdiDevRun {
     int8_t *spins;                   // [R][N] spins in rank space
     const uint32_t *tab;             // threshold rows (see gdi_api.cpp: build_table)
     const int32_t *tab_off;          // [M+1] row offsets into tab
+    const float *temp;               // [M] T_s (Metropolis; only guides the E* search)
     int32_t mode;                    // 0 Metropolis, 1 paper P_f
     int32_t sweeps;                  // M
     int32_t s_begin, s_end;
@@ -49,6 +66,13 @@ int gdi_launch_init(const GdiDevProblem &P, int8_t *spins, const int8_t *init_or
 int gdi_launch_cta_anneal(const GdiDevProblem &P, const GdiDevRun &R, int block, int grid_limit,
                           void *stream, int *grid_used, size_t *smem_used);
 int gdi_cta_smem_bytes(const GdiDevProblem &P, const GdiDevRun &R, int block, size_t *bytes, int *hist);
+int gdi_grid_plan(const GdiDevProblem &P, int max_row, int sms, int *spc, int *wpc, size_t *smem);
+size_t gdi_grid_smem(int spc, int wpc, int P, int max_row);
+int gdi_grid_fallback_fits(int spc);
+int gdi_launch_grid_anneal(const GdiDevProblem &P, const GdiDevRun &R, const GdiGridScratch &X,
+                           int8_t *spins, int sms, int spc, int wpc, size_t smem, void *stream);
+int gdi_launch_grid_finish(const GdiDevProblem &P, const GdiDevRun &R, const GdiGridScratch &X,
+                           int8_t *spins, int do_repair, void *stream);
 int gdi_launch_gather_spins(const GdiDevProblem &P, const int8_t *spins_rank, int8_t *out_orig,
                             void *stream);
 
@@ -58,3 +82,6 @@ int gdi_launch_gather_spins(const GdiDevProblem &P, const int8_t *spins_rank, in
 
 // device error codes written to GdiDevRun::err
 #define GDI_DEVERR_RANGE 1
+#define GDI_DEVERR_TIMEOUT 2
+
+#define GDI_GRID_TW 129   // entries of a window table (2 * 64 + 1)
