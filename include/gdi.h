@@ -154,6 +154,45 @@ int gdi_last_launch(gdi_ctx *ctx, int32_t *path, int32_t *grid, int64_t *smem_by
  * the largest degree, and the E_cap of the last schedule (0 before any anneal). */
 int gdi_info(gdi_ctx *ctx, int32_t *num_classes, int32_t *max_degree, int32_t *ecap);
 
+/* ---- Allocation-free sweep (the paper has no counterpart) -----------------------------------
+ * For callers that cannot allocate device memory while they run: code whose device memory belongs
+ * to another allocator (a framework's caching pool or a fixed arena) or that must not grow its
+ * device footprint after start-up.  gdi_anneal allocates its table, staging and scratch buffers on
+ * first use; gdi_anneal_static calls no cudaMalloc, cudaFree or allocating library routine.  It
+ * runs the grid-scale sweep kernel of GDI_PATH_GRID on one graph whose arrays the caller already
+ * holds on the device, in the rank-space layout below, with its scratch in one fixed-size static
+ * device array of about 1.4 MB that every GPU which loads libgdi.so keeps until the process exits.
+ *
+ * Inputs (device pointers, current device, read only):
+ *   row_ptr   [n + 1] int64 CSR offsets of the graph relabelled in rank order (vertices sorted by
+ *             colour, then id); col [row_ptr[n]] neighbour rank | 0x80000000 when the weight is -1.
+ *   class_ptr [num_classes + 1] rank boundaries of the colour classes (0 ... n); max_class is the
+ *             largest class, max_degree the largest row length.
+ *   tab, tab_off [sweeps + 1], temp [sweeps]: the threshold table (Metropolis: row s holds
+ *             floor(exp(-dE / T_s) 2^32) for dE = 1, 2, ... while non-zero, temp[s] = T_s; paper
+ *             mode: row s holds 2^32 - p_s, 2^31, p_s), max_row its longest row.
+ *   A, B, W, mode, sweeps, [first_sweep, last_sweep) (last_sweep <= 0 = sweeps), seed: as in
+ *   gdi_model / gdi_schedule / gdi_run; replicas 1..8 draw Philox counters (rank/4, sweep, 0, r).
+ * In/out: spins [replicas][n] int8 (+1/-1) in rank order, annealed in place (no repair).
+ * Out: G_out [replicas] int32, the magnetisation after the last sweep.
+ * Limits: n <= GDI_STATIC_MAX_VERTICES, replicas <= 8, W >= 1 and small enough for the per-block
+ * plan, at most GDI_STATIC_MAX_BLOCKS blocks; beyond them the call returns GDI_ERR_TOO_LARGE and
+ * launches nothing.  Enqueued on `stream`; returns without waiting.
+ * The first call on a device looks up the device address of the static array
+ * (cudaGetSymbolAddress), so make that first call before any stream capture.  Every call shares
+ * the one array, which keeps the previous call's contents (the call clears what must start at
+ * zero): calls whose work overlaps on the GPU race with each other, so serialise them (one stream,
+ * or events).  If a grid barrier wait ever ran out, the kernel stops early and the spins are those
+ * of the interrupted sweep. */
+#define GDI_STATIC_MAX_VERTICES (1 << 20)
+#define GDI_STATIC_MAX_BLOCKS 160
+int gdi_anneal_static(int32_t n, const int64_t *row_ptr, const uint32_t *col, int32_t num_classes,
+                      const int32_t *class_ptr, int32_t max_class, int32_t max_degree, int32_t A,
+                      int32_t B, int32_t W, int32_t mode, const uint32_t *tab,
+                      const int32_t *tab_off, const float *temp, int32_t max_row, int32_t sweeps,
+                      int32_t first_sweep, int32_t last_sweep, uint64_t seed, int32_t replicas,
+                      int8_t *spins, int32_t *G_out, void *stream);
+
 /* Free the context and its device buffers (synchronises the run stream first). */
 void gdi_destroy(gdi_ctx *ctx);
 

@@ -27,7 +27,7 @@ ERRORS = {
 # every entry point that include/gdi.h declares
 EXPORTS = ["gdi_create", "gdi_anneal", "gdi_get_spins", "gdi_get_results", "gdi_cut", "gdi_balance",
            "gdi_get_trace", "gdi_configure", "gdi_last_launch", "gdi_info", "gdi_destroy",
-           "gdi_strerror", "gdi_last_error"]
+           "gdi_strerror", "gdi_last_error", "gdi_anneal_static"]
 GDI_PATH_AUTO, GDI_PATH_CTA, GDI_PATH_GRID = 0, 1, 2
 
 
@@ -79,6 +79,8 @@ def load():
     L.gdi_get_trace.argtypes = [vp, vp, vp, vp]
     L.gdi_info.argtypes = [vp, vp, vp, vp]
     L.gdi_configure.argtypes = [vp, i32, i32, i32]
+    L.gdi_anneal_static.argtypes = [i32, vp, vp, i32, vp, i32, i32, i32, i32, i32, i32, vp, vp, vp,
+                                    i32, i32, i32, i32, C.c_uint64, i32, vp, vp, vp]
     L.gdi_last_launch.argtypes = [vp, vp, vp, vp, vp]
     L.gdi_destroy.argtypes = [vp]
     L.gdi_destroy.restype = None

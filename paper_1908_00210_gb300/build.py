@@ -9,7 +9,7 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 LIB = os.path.join(PKG, "libgdi.so")
-SOURCES = ["gdi_kernels.cu", "gdi_grid.cu", "gdi_api.cpp"]
+SOURCES = ["gdi_kernels.cu", "gdi_grid.cu", "gdi_static.cu", "gdi_api.cpp"]
 HEADERS = ["gdi_internal.h", "gdi_device.cuh", os.path.join(ROOT, "include", "gdi.h")]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
@@ -33,7 +33,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         return LIB
     tmp = LIB + f".tmp{os.getpid()}"
     cmd = [_nvcc(), ARCH, "-O3", "-lineinfo", "-std=c++17", "-shared", "-Xcompiler", "-fPIC",
-           "-Xcompiler", "-O2", "--threads", "2", "-I", os.path.join(ROOT, "include"), "-I", CSRC,
+           "-Xcompiler", "-O2", "--threads", "4", "-I", os.path.join(ROOT, "include"), "-I", CSRC,
            "-o", tmp] + [os.path.join(CSRC, s) for s in SOURCES] + ["-cudart", "shared"]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")

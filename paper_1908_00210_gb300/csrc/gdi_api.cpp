@@ -55,6 +55,8 @@ struct DevBuf {
 
 }  // namespace
 
+int gdi_set_error(int code, const std::string &msg) { return fail(code, msg); }
+
 struct gdi_ctx {
     int device = 0;
     int32_t Q = 0, R = 1, A = 0, B = 1, W = 0;

@@ -60,6 +60,12 @@ struct GdiDevRun {
     int32_t *err;                    // device error word (0 = ok)
 };
 
+// record a failure for gdi_last_error() (gdi_api.cpp); returns code
+#ifdef __cplusplus
+#include <string>
+int gdi_set_error(int code, const std::string &msg);
+#endif
+
 // kernel launch wrappers (gdi_kernels.cu); return a cudaError_t as int
 int gdi_launch_init(const GdiDevProblem &P, int8_t *spins, const int8_t *init_orig, int init_kind,
                     uint32_t key0, uint32_t key1, void *stream);
