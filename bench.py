@@ -27,7 +27,7 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 
 # ---------------------------------------------------------------------------------------------
-# Workloads (synthetic stand-ins for the paper's G-set graphs; see the design doc for the recipes)
+# Workloads: seeded synthetic stand-ins for the paper's G-set graphs (generators in gdi_synth)
 WORKLOADS = {
     # Barabasi-Albert n = 10^6, m = 5, unit weights, greedy colouring (6 classes), 8 replicas,
     # 500 sweeps, window W = 256: the grid-scale path (every SM on one graph)
@@ -309,7 +309,7 @@ def run_ours(args, wl, rank, world, local):
         achieved = rf["ops_per_update"] * rate / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
                 "frac": achieved / peak, "traffic": None, "ops_per_update": rf["ops_per_update"],
-                "peak_note": "SMs x 128 int32 lanes x max SM clock (derived, see DESIGN.md)"}
+                "peak_note": "SMs x 128 int32 lanes x max SM clock (derived)"}
     try:
         if args.quick:
             raise RuntimeError("skipped (--quick)")

@@ -2,7 +2,7 @@
  * gdi.h -- C ABI of libgdi.so, a GB300 (sm_103a) implementation of the Globally Decoupled Ising
  * (GDI) annealer for balanced min-cut graph bisection (Cook, Jin, Tan, arXiv:1908.00210).
  *
- * Problem (Section 3.1): split the vertices of G(V, E) into V1 (spin +1) and V2 (spin -1) with
+ * Problem (Section 4.1): split the vertices of G(V, E) into V1 (spin +1) and V2 (spin -1) with
  * |V1| = |V2| and the smallest total weight of crossing edges.  The annealer minimises
  *     H = A (sum_i s_i)^2 + B sum_<ij> w_ij (1 - s_i s_j) / 2              (Eq. 4, 5, 6)
  * with Algorithm 3: the balance term reads one global magnetisation G = sum_i s_i that is updated
@@ -85,7 +85,7 @@ typedef struct {
     int32_t replicas;   /* independent replicas per instance, >= 1                              */
 } gdi_model;
 
-/* Annealing schedule (Section 4.2; "reduce P_f" of Alg. 2/3 is the per-sweep table row). */
+/* Annealing schedule (Section 5.2; "reduce P_f" of Alg. 2/3 is the per-sweep table row). */
 typedef struct {
     int32_t mode;       /* GDI_METROPOLIS or GDI_PAPER_PF                                         */
     double t0, t1;      /* Metropolis temperatures at the first and last sweep, > 0              */
@@ -119,11 +119,11 @@ int gdi_create(gdi_ctx **out, const gdi_graph *graph, const gdi_model *model);
 int gdi_anneal(gdi_ctx *ctx, const gdi_schedule *schedule, const gdi_run *run);
 
 /* Spins after the last gdi_anneal, [replicas][N] in original vertex order (+1 = V1, -1 = V2,
- * Section 3.1).  Synchronises the run stream. */
+ * Section 4.1).  Synchronises the run stream. */
 int gdi_get_spins(gdi_ctx *ctx, int8_t *out, int32_t out_mem);
 
 /* Per (instance, replica), index q * replicas + r: raw G after the last sweep, G after repair,
- * cut before and after repair (cut = sum of crossing edge weights, Section 5).  Any pointer may be
+ * cut before and after repair (cut = sum of crossing edge weights, Section 6.2).  Any pointer may be
  * NULL.  Host pointers.  Synchronises the run stream. */
 int gdi_get_results(gdi_ctx *ctx, int32_t *raw_G, int32_t *final_G, int64_t *raw_cut,
                     int64_t *final_cut);

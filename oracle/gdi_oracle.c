@@ -16,7 +16,7 @@
  *   - Algorithm 3 (GDI): G is computed once before the first sweep and then updated by the
  *     change of each flipped spin; every spin decides from G and its neighbours only.
  *   - the noise: a per-temperature integer acceptance threshold table (Metropolis form, or the
- *     paper's argmin-then-random-flip-with-P_f form, Section 4.2 and Alg. 2/3), drawn with the
+ *     paper's argmin-then-random-flip-with-P_f form, Section 5.2 and Alg. 2/3), drawn with the
  *     counter-based Philox4x32-10 generator (Salmon et al., SC'11) in place of cuRAND.
  *
  * Readings of the paper taken here (the paper leaves these open or garbles them):
@@ -34,7 +34,7 @@
  *       first, the way the earliest atomics would.
  *   R3  One draw per spin per sweep merges "argmin" and "flip with probability P_f" into a single
  *       Bernoulli decision with the same probabilities (flip w.p. 1-P_f if dE<0, 1/2 if dE=0, P_f
- *       if dE>0); "flip iff u <= P_f" (Section 4.2) becomes u32 < floor(P_f 2^32) + 1.
+ *       if dE>0); "flip iff u <= P_f" (Section 5.2) becomes u32 < floor(P_f 2^32) + 1.
  *   R4  Balanced random initial spins: ranks are paired (2p, 2p+1) and a Philox coin gives the
  *       pair (+1,-1) or (-1,+1); an odd last rank starts at -1.
  *   R5  After the last sweep an exact-balance repair flips the k = (|G| - (n mod 2))/2 majority

@@ -114,7 +114,7 @@ def _stream_handle(stream):
 
 @dataclass
 class Schedule:
-    """Annealing schedule (Section 4.2): Metropolis T geometric t0 -> t1, or the paper's P_f."""
+    """Annealing schedule (Section 5.2): Metropolis T geometric t0 -> t1, or the paper's P_f."""
     sweeps: int
     t0: float = 3.0
     t1: float = 0.05

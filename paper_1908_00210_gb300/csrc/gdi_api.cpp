@@ -142,7 +142,7 @@ namespace {
 // Threshold table.  Metropolis row s holds thr_s(dE) = floor(exp(-dE / T_s) 2^32) for dE = 1, 2, ...
 // while it is non-zero (thr = 2^32 for dE <= 0 is implicit); T_s = t0 (t1/t0)^(s/(M-1)).
 // Paper row s holds thr for dE = -1, 0, +1: 2^32 - p, 2^31, p with p = floor(P_f,s 2^32) + 1
-// (argmin, then the random flip "u <= P_f" of Section 4.2), P_f,s = pf0 (pf1/pf0)^(s/(M-1)).
+// (argmin, then the random flip "u <= P_f" of Section 5.2), P_f,s = pf0 (pf1/pf0)^(s/(M-1)).
 double sched_at(double v0, double v1, int s, int M)
 {
     if (M <= 1 || v0 == v1) return v0;

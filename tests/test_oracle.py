@@ -104,7 +104,7 @@ def test_metropolis_table_closed_form():
 
 def test_paper_pf_table_closed_form():
     """Paper mode (Alg. 2/3): argmin then random flip with P_f; P_f decays geometrically;
-    'flip iff u <= P_f' (Section 4.2)."""
+    'flip iff u <= P_f' (Section 5.2)."""
     M, pf0, pf1 = 20, 0.2, 0.002
     ecap, thr = oracle.table(oracle.PAPER_PF, 0, 0, pf0, pf1, M)
     assert ecap == 1
@@ -114,7 +114,7 @@ def test_paper_pf_table_closed_form():
         assert thr[s, 2] == p                     # dE > 0: only the random flip
         assert thr[s, 1] == 2 ** 31               # dE = 0: tie broken at random (Eq. 2)
         assert thr[s, 0] == 2 ** 32 - p           # dE < 0: argmin flips unless undone
-    # the worked example of Section 4.2: 500 nodes, N_rf = 100 -> P_f = 0.20
+    # the worked example of Section 5.2: 500 nodes, N_rf = 100 -> P_f = 0.20
     _, thr0 = oracle.table(oracle.PAPER_PF, 0, 0, 100 / 500, 100 / 500, 1)
     assert abs(int(thr0[0, 2]) / 2 ** 32 - 0.20) < 1e-9
 
