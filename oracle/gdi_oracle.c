@@ -25,7 +25,9 @@
  *       as adding the change of s_i (+-2 or 0), so G stays exact after every update.
  *   R2  Determinism in place of the GPU race: vertices are updated colour class by colour class
  *       (a class has no internal edges, so every h_i inside a class is fixed while the class is
- *       updated).  A class is cut into windows of W consecutive ranks (W = 0: the whole class).
+ *       updated); inside a class the rank order is that of splitmix64(vertex id), a fixed
+ *       pseudo-random order.  A class is cut into windows of W consecutive ranks (W = 0: the whole
+ *       class).
  *       Inside a window every spin sees the exact running G, in a canonical order: first the
  *       spins that were +1 at window start, sorted by their flip threshold gamma ascending (rank
  *       ascending on ties), then the spins that were -1, sorted by gamma' descending (rank
@@ -198,6 +200,17 @@ int oracle_greedy_color(int32_t n, const int64_t *row_ptr, const int32_t *col, i
 }
 
 /* ------------------------------------------------------------------------------------------ */
+typedef struct {
+    uint64_t key;
+    int32_t v;
+} hash_item;
+
+static int cmp_hash(const void *a, const void *b)
+{
+    const hash_item *x = (const hash_item *)a, *y = (const hash_item *)b;
+    return (x->key > y->key) - (x->key < y->key);
+}
+
 typedef struct {
     int64_t key;      /* gamma (or -gamma' for the -1 group) */
     int32_t rank;
@@ -397,7 +410,8 @@ int oracle_anneal(const oracle_params *p, oracle_out *o)
         for (int64_t e = p->row_ptr[v]; e < p->row_ptr[v + 1]; ++e)
             if (color[p->col[e]] == color[v]) { rc = ORC_ERR_COLOR; goto done; }
 
-    /* rank order: (colour asc, id asc) -- counting sort by colour, stable in id */
+    /* rank order: (colour asc, splitmix64(id) asc) -- counting sort by colour, then each class
+     * sorted by the hash of the vertex id (R2: a fixed pseudo-random order inside a class) */
     {
         int32_t *cnt = (int32_t *)calloc((size_t)ncol + 1, sizeof(int32_t));
         if (!cnt) { rc = ORC_ERR_OOM; goto done; }
@@ -408,11 +422,17 @@ int oracle_anneal(const oracle_params *p, oracle_out *o)
             if (cnt[c + 1] > cnt[c]) cls_lo[nclass++] = cnt[c];
         cls_lo[nclass] = n;
         o->num_colors = nclass;
-        for (int32_t v = 0; v < n; ++v) {
-            const int32_t r = cnt[color[v]]++;
-            rank[v] = r;
-            vert[r] = v;
+        for (int32_t v = 0; v < n; ++v) vert[cnt[color[v]]++] = v;
+        for (int32_t k = 0; k < nclass; ++k) {
+            const int32_t lo = cls_lo[k], hi = cls_lo[k + 1];
+            hash_item *hi_items = (hash_item *)malloc(sizeof(hash_item) * (size_t)(hi - lo));
+            if (!hi_items) { free(cnt); rc = ORC_ERR_OOM; goto done; }
+            for (int32_t r = lo; r < hi; ++r) { hi_items[r - lo].key = mix64((uint64_t)vert[r]); hi_items[r - lo].v = vert[r]; }
+            qsort(hi_items, (size_t)(hi - lo), sizeof(hash_item), cmp_hash);
+            for (int32_t r = lo; r < hi; ++r) vert[r] = hi_items[r - lo].v;
+            free(hi_items);
         }
+        for (int32_t r = 0; r < n; ++r) rank[vert[r]] = r;
         free(cnt);
     }
     const int32_t nclass = o->num_colors;

@@ -57,6 +57,17 @@ struct DevBuf {
 
 int gdi_set_error(int code, const std::string &msg) { return fail(code, msg); }
 
+namespace {
+// splitmix64 finaliser (Steele, Lea, Flood 2014): the in-class rank key
+uint64_t splitmix64_host(uint64_t z)
+{
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+}  // namespace
+
 struct gdi_ctx {
     int device = 0;
     int32_t Q = 0, R = 1, A = 0, B = 1, W = 0;
@@ -361,9 +372,25 @@ int gdi_create(gdi_ctx **out, const gdi_graph *g, const gdi_model *m)
         c->num_classes[(size_t)q] = nclass;
         for (int64_t v = lo; v < hi; ++v) {
             const int32_t r = cnt[(size_t)color[(size_t)v]]++;
-            rank_of[(size_t)v] = (int32_t)(lo + r);
             vert_of[(size_t)(lo + r)] = (int32_t)v;
         }
+        // inside a class, ranks follow splitmix64 of the local vertex id (a fixed pseudo-random
+        // order, so that heavy vertices spread over windows and blocks)
+        {
+            std::vector<std::pair<uint64_t, int32_t>> keyed;
+            const int32_t *bounds = class_ptr.data() + class_off[(size_t)q];
+            for (int32_t k = 0; k < nclass; ++k) {
+                const int32_t c0 = bounds[k], c1 = bounds[k + 1];
+                keyed.resize((size_t)(c1 - c0));
+                for (int32_t r = c0; r < c1; ++r) {
+                    const int32_t v = vert_of[(size_t)(lo + r)];
+                    keyed[(size_t)(r - c0)] = {splitmix64_host((uint64_t)(v - lo)), v};
+                }
+                std::sort(keyed.begin(), keyed.end());
+                for (int32_t r = c0; r < c1; ++r) vert_of[(size_t)(lo + r)] = keyed[(size_t)(r - c0)].second;
+            }
+        }
+        for (int64_t r = lo; r < hi; ++r) rank_of[(size_t)vert_of[(size_t)r]] = (int32_t)r;
         c->max_n = std::max(c->max_n, n);
     }
     class_off[(size_t)Q] = (int32_t)class_ptr.size();

@@ -41,6 +41,8 @@ constexpr int16_t TINV = INT16_MIN;
 constexpr int LONG_ROW = 48;
 constexpr long long SPIN_LIMIT = 1ll << 26;
 
+__device__ __forceinline__ int warp_id() { return threadIdx.x >> 5; }
+
 __device__ __forceinline__ uint64_t spread8(uint32_t b)
 {
     return (((uint64_t)(b & 0x7Fu) * 0x0002040810204081ull) & 0x0101010101010101ull) |
@@ -122,7 +124,8 @@ __device__ bool grid_sync(const GdiGridScratch &X)
     return ok != 0;
 }
 
-// local fields of one rank for all 8 replicas (thread-serial over the row)
+// local fields of one rank for all 8 replicas (thread-serial over the row, four neighbours in
+// flight at a time)
 __device__ void field8_thread(const GdiDevProblem &P, int64_t base, int32_t r, const uint8_t *packed,
                               int32_t h[8])
 {
@@ -131,12 +134,21 @@ __device__ void field8_thread(const GdiDevProblem &P, int64_t base, int32_t r, c
     int32_t cP[8], cN[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) { cP[k] = 0; cN[k] = 0; }
-    int32_t nP = 0, nN = 0, cnt = 0;
-    for (int64_t e = e0; e < e1; ++e) {
-        const uint32_t c = __ldg(P.col + e);
-        const uint64_t s = spread8(__ldcg(packed + base + (c & 0x7FFFFFFFu)));
-        if (c >> 31) { aN += s; ++nN; } else { aP += s; ++nP; }
-        if (++cnt == 255) {
+    int32_t nN = 0, cnt = 0;
+    int64_t e = e0;
+    for (; e + 4 <= e1; e += 4) {
+        const uint32_t c0 = __ldg(P.col + e), c1 = __ldg(P.col + e + 1);
+        const uint32_t c2 = __ldg(P.col + e + 2), c3 = __ldg(P.col + e + 3);
+        const uint64_t s0 = spread8(__ldcg(packed + base + (c0 & 0x7FFFFFFFu)));
+        const uint64_t s1 = spread8(__ldcg(packed + base + (c1 & 0x7FFFFFFFu)));
+        const uint64_t s2 = spread8(__ldcg(packed + base + (c2 & 0x7FFFFFFFu)));
+        const uint64_t s3 = spread8(__ldcg(packed + base + (c3 & 0x7FFFFFFFu)));
+        if (c0 >> 31) { aN += s0; ++nN; } else aP += s0;
+        if (c1 >> 31) { aN += s1; ++nN; } else aP += s1;
+        if (c2 >> 31) { aN += s2; ++nN; } else aP += s2;
+        if (c3 >> 31) { aN += s3; ++nN; } else aP += s3;
+        cnt += 4;
+        if (cnt >= 252) {
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
                 cP[k] += (int32_t)((aP >> (8 * k)) & 0xFF);
@@ -146,6 +158,12 @@ __device__ void field8_thread(const GdiDevProblem &P, int64_t base, int32_t r, c
             cnt = 0;
         }
     }
+    for (; e < e1; ++e) {
+        const uint32_t c = __ldg(P.col + e);
+        const uint64_t sv = spread8(__ldcg(packed + base + (c & 0x7FFFFFFFu)));
+        if (c >> 31) { aN += sv; ++nN; } else aP += sv;
+    }
+    const int32_t nP = (int32_t)(e1 - e0) - nN;
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
         cP[k] += (int32_t)((aP >> (8 * k)) & 0xFF);
@@ -154,39 +172,66 @@ __device__ void field8_thread(const GdiDevProblem &P, int64_t base, int32_t r, c
     }
 }
 
-// the same for one long row, by a whole warp; the result is valid in every lane
-__device__ void field8_warp(const GdiDevProblem &P, int64_t base, int32_t r, const uint8_t *packed,
-                            int32_t h[8])
+// Partial sums of one chunk [c0, c1) of a long row, by one warp: sw = sum of weights,
+// sb[k] = sum of w * bit_k (bit_k set = replica k is -1); valid in every lane.
+__device__ void chunk8_warp(const GdiDevProblem &P, int64_t base, int64_t c0, int64_t c1,
+                            const uint8_t *packed, int32_t &sw, int32_t sb[8])
 {
     const int lane = threadIdx.x & 31;
-    const int64_t e0 = P.row_ptr[base + r], e1 = P.row_ptr[base + r + 1];
     uint64_t aP = 0, aN = 0;
-    int32_t cP[8], cN[8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) { cP[k] = 0; cN[k] = 0; }
-    int32_t nP = 0, nN = 0, cnt = 0;
-    for (int64_t e = e0 + lane; e < e1; e += 32) {
-        const uint32_t c = __ldg(P.col + e);
-        const uint64_t s = spread8(__ldcg(packed + base + (c & 0x7FFFFFFFu)));
-        if (c >> 31) { aN += s; ++nN; } else { aP += s; ++nP; }
-        if (++cnt == 255) {
-#pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                cP[k] += (int32_t)((aP >> (8 * k)) & 0xFF);
-                cN[k] += (int32_t)((aN >> (8 * k)) & 0xFF);
-            }
-            aP = aN = 0;
-            cnt = 0;
-        }
+    int32_t nN = 0, n = 0;
+    // at most ceil(1024 / 32) = 32 entries per lane: byte lanes cannot overflow
+    int64_t e = c0 + lane;
+    for (; e + 96 < c1; e += 128) {
+        const uint32_t x0 = __ldg(P.col + e), x1 = __ldg(P.col + e + 32);
+        const uint32_t x2 = __ldg(P.col + e + 64), x3 = __ldg(P.col + e + 96);
+        const uint64_t s0 = spread8(__ldcg(packed + base + (x0 & 0x7FFFFFFFu)));
+        const uint64_t s1 = spread8(__ldcg(packed + base + (x1 & 0x7FFFFFFFu)));
+        const uint64_t s2 = spread8(__ldcg(packed + base + (x2 & 0x7FFFFFFFu)));
+        const uint64_t s3 = spread8(__ldcg(packed + base + (x3 & 0x7FFFFFFFu)));
+        if (x0 >> 31) { aN += s0; ++nN; } else aP += s0;
+        if (x1 >> 31) { aN += s1; ++nN; } else aP += s1;
+        if (x2 >> 31) { aN += s2; ++nN; } else aP += s2;
+        if (x3 >> 31) { aN += s3; ++nN; } else aP += s3;
+        n += 4;
     }
-    nP = warp_sum(nP);
-    nN = warp_sum(nN);
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-        const int32_t p = warp_sum(cP[k] + (int32_t)((aP >> (8 * k)) & 0xFF));
-        const int32_t q = warp_sum(cN[k] + (int32_t)((aN >> (8 * k)) & 0xFF));
-        h[k] = (nP - nN) - 2 * (p - q);
+    for (; e < c1; e += 32) {
+        const uint32_t x = __ldg(P.col + e);
+        const uint64_t sv = spread8(__ldcg(packed + base + (x & 0x7FFFFFFFu)));
+        if (x >> 31) { aN += sv; ++nN; } else aP += sv;
+        ++n;
     }
+    sw = warp_sum(n - 2 * nN);
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+        sb[k] = warp_sum((int32_t)((aP >> (8 * k)) & 0xFF) - (int32_t)((aN >> (8 * k)) & 0xFF));
+}
+
+// In-place cumulative counts of bins[0, nb) by one warp: forward (bins[x] = base + sum_{b <= x})
+// or backward (bins[x] = base + sum_{b >= x}); each lane scans a contiguous chunk.
+__device__ void warp_cumulate(int32_t *bins, int nb, int32_t base, bool forward)
+{
+    const int lane = threadIdx.x & 31;
+    const int ch = (nb + 31) / 32;
+    const int l = forward ? lane : 31 - lane;          // chunk order along the scan direction
+    const int b0 = l * ch, b1 = min(b0 + ch, nb);
+    int32_t loc = 0;
+    for (int b = b0; b < b1; ++b) loc += bins[b];
+    // lanes in increasing order hold the chunks in scan order (backward: lane 0 owns the top
+    // chunk), so an inclusive scan over lane order gives the sum up to and including my chunk
+    int32_t x = loc;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+        if (lane >= o) x += y;
+    }
+    int32_t run = base + x - loc;                       // everything before my chunk
+    if (forward) {
+        for (int b = b0; b < b1; ++b) { run += bins[b]; bins[b] = run; }
+    } else {
+        for (int b = b1 - 1; b >= b0; --b) { run += bins[b]; bins[b] = run; }
+    }
+    __syncwarp();
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -235,15 +280,7 @@ __device__ int32_t warp_group(const int32_t *gam, int gs, int gc, const uint8_t 
     __syncwarp();
     // cumulative counts toward the deep side: plus: C(base + x) = deep + sum_{b <= x};
     // minus: D(base + x) = deep + sum_{b >= x}
-    if (lane == 0) {
-        int32_t run = deep;
-        if (plus) {
-            for (int b = 0; b < HA; ++b) { run += bins[b]; bins[b] = run; }
-        } else {
-            for (int b = HA - 1; b >= 0; --b) { run += bins[b]; bins[b] = run; }
-        }
-    }
-    __syncwarp();
+    warp_cumulate(bins, HA, deep, plus);
     // K = #{k : count(g -/+ 2k) >= k + 1}, k in [0, KC] (one lane per k)
     int32_t K;
     int64_t vstar = 0;
@@ -401,14 +438,47 @@ __device__ void range_thresholds(const GridArgs &A, const GSmem &S, int32_t a0, 
     }
     __syncthreads();
     if (all_reps) {
+        // long rows: chunks of 1024 entries are warp tasks; partial sums meet in shared memory.
+        // acc[i*8 + k] = sum_j w_ij bit_k(j) lives in the threshold array (free until the
+        // thresholds are written below); sum_j w_ij lives in the first 4 bytes of the row's
+        // field slots; the chunk count of long row t is kept in the histogram area.
         const int nl = nlong;
-        for (int t = threadIdx.x >> 5; t < nl; t += NWARP) {
+        int32_t *acc = gam_out;
+        int32_t *nchunk = S.hist;                // [nl] (spc <= NWARP * 2 * HB, checked by the plan)
+        for (int t = threadIdx.x; t < nl; t += GB) {
             const int32_t i = S.longq[t];
-            int32_t h[8];
-            field8_warp(P, base, a0 + i, packed, h);
-            if ((threadIdx.x & 31) == 0)
+            const int64_t deg = P.row_ptr[base + a0 + i + 1] - P.row_ptr[base + a0 + i];
+            nchunk[t] = (int32_t)((deg + 1023) / 1024);
 #pragma unroll
-                for (int k = 0; k < 8; ++k) hbuf[(size_t)i * 8 + k] = (int16_t)h[k];
+            for (int k = 0; k < 8; ++k) acc[(size_t)i * 8 + k] = 0;
+            *reinterpret_cast<int32_t *>(hbuf + (size_t)i * 8) = 0;
+        }
+        __syncthreads();
+        {
+            int task = 0;
+            for (int t = 0; t < nl; ++t) {
+                const int nc = nchunk[t];
+                for (int c = 0; c < nc; ++c, ++task) {
+                    if (task % NWARP != warp_id()) continue;
+                    const int32_t i = S.longq[t];
+                    const int64_t r0 = P.row_ptr[base + a0 + i], r1 = P.row_ptr[base + a0 + i + 1];
+                    const int64_t c0 = r0 + (int64_t)c * 1024, c1 = min(r1, c0 + 1024);
+                    int32_t swv, sb[8];
+                    chunk8_warp(P, base, c0, c1, packed, swv, sb);
+                    if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+                        for (int k = 0; k < 8; ++k) atomicAdd(&acc[(size_t)i * 8 + k], sb[k]);
+                        atomicAdd(reinterpret_cast<int32_t *>(hbuf + (size_t)i * 8), swv);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < nl; t += GB) {
+            const int32_t i = S.longq[t];
+            const int32_t swv = *reinterpret_cast<const int32_t *>(hbuf + (size_t)i * 8);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) hbuf[(size_t)i * 8 + k] = (int16_t)(swv - 2 * acc[(size_t)i * 8 + k]);
         }
         __syncthreads();
     }
@@ -460,27 +530,24 @@ __device__ void window_table(const GSmem &S, int ws, int we, int r, int32_t c, b
     under = warp_sum(under);
     over = warp_sum(over);
     __syncwarp();
-    if (lane == 0) {
-        int32_t run = under;
-        for (int b = 0; b < HB; ++b) { run += hp[b]; hp[b] = run; }          // C(base + b)
-        run = over;
-        for (int b = HB - 1; b >= 0; --b) { run += hm[b]; hm[b] = run; }     // D(base + b)
-    }
-    __syncwarp();
+    warp_cumulate(hp, HB, under, true);     // C(base + b)
+    warp_cumulate(hm, HB, over, false);     // D(base + b)
     for (int e = lane; e < TW; e += 32) {
         int64_t g = (int64_t)c - RT + e;
         bool valid = true;
         for (int ph = 0; ph < 2 && valid; ++ph) {
             const bool plus = plus_first ? (ph == 0) : (ph == 1);
-            int32_t K = 0;
-            bool capped = true;
-            for (int k = 0; k <= KC; ++k) {
-                const int64_t v = plus ? g - 2 * k : g + 2 * k;
-                const int64_t x = v - base;
-                const int32_t cnt = plus ? hp[x] : hm[x];
-                if (cnt >= k + 1) K = k + 1; else { capped = false; break; }
+            // K = #{k in [0, KC] : count(g -/+ 2k) >= k + 1}; the predicate holds for a prefix of
+            // k, so K is found by binary search; K = KC + 1 means the table cannot represent it
+            int32_t lo = 0, hi = KC + 1;
+            while (lo < hi) {
+                const int32_t mid = (lo + hi + 1) >> 1;          // does k = mid - 1 hold?
+                const int64_t v = plus ? g - 2 * (mid - 1) : g + 2 * (mid - 1);
+                const int32_t cnt = plus ? hp[v - base] : hm[v - base];
+                if (cnt >= mid) lo = mid; else hi = mid - 1;
             }
-            if (capped) valid = false;
+            const int32_t K = lo;
+            if (K > KC) valid = false;
             g = plus ? g - 2 * K : g + 2 * K;
         }
         tab[e] = valid ? (int16_t)(g - ((int64_t)c - RT)) : TINV;
@@ -585,9 +652,15 @@ __global__ void __launch_bounds__(GB, 1) gdi_grid_anneal_kernel(GridArgs A)
             // ---- phase C: one block per replica chains the block tables
             if (p < nrep) {
                 const int r = p;
-                for (int64_t t = threadIdx.x; t < (int64_t)Pb * TW; t += GB) {
-                    const int pp = (int)(t / TW), e = (int)(t % TW);
-                    S.ctab[(size_t)pp * TW + e] = __ldcg(X.tables + ((size_t)pp * 8 + r) * TW + e);
+                for (int pp = warp; pp < Pb; pp += NWARP) {
+                    const int16_t *src = X.tables + ((size_t)pp * 8 + r) * TW;
+                    int16_t v[(TW + 31) / 32];
+#pragma unroll
+                    for (int j = 0; j < (TW + 31) / 32; ++j)
+                        v[j] = (lane + 32 * j < TW) ? __ldcg(src + lane + 32 * j) : (int16_t)0;
+#pragma unroll
+                    for (int j = 0; j < (TW + 31) / 32; ++j)
+                        if (lane + 32 * j < TW) S.ctab[(size_t)pp * TW + lane + 32 * j] = v[j];
                 }
                 const int32_t c0 = Gc[r];
                 if (threadIdx.x == 0) { chain_pp = 0; chain_g = c0; }
@@ -905,7 +978,8 @@ int gdi_grid_fallback_fits(int spc)
 {
     // the exact chain fallback keeps thresholds, fields, start signs and bins of one block's
     // windows (one replica) in the histogram area
-    return (size_t)spc * 7 + 64 + HA * sizeof(int32_t) <= (size_t)NWARP * 2 * HB * sizeof(int32_t);
+    return (size_t)spc * 7 + 64 + HA * sizeof(int32_t) <= (size_t)NWARP * 2 * HB * sizeof(int32_t) &&
+           (size_t)spc <= (size_t)NWARP * 2 * HB;
 }
 
 int gdi_grid_plan(const GdiDevProblem &P, int max_row, int sms, int *spc, int *wpc, size_t *smem)

@@ -183,7 +183,10 @@ def test_bruteforce_known_bisection_widths():
 
 # ---------------------------------------------------------------- the annealer ---------------
 def _rank_order(g, color):
-    return np.lexsort((np.arange(g.n), color))   # vertices sorted by (colour, id)
+    """Vertices sorted by (colour, splitmix64(id)): the in-class order of reading R2."""
+    from gdi_synth import splitmix64
+    key = splitmix64(np.arange(g.n, dtype=np.uint64))
+    return np.lexsort((key, color))
 
 
 def _draw(seed, r, sweep, inst, rep):

@@ -20,8 +20,10 @@ pytestmark = pytest.mark.gpu
 
 
 def rank_space(g, color):
-    """Rank order (colour asc, id asc) and the rank-space CSR in the layout of include/gdi.h."""
-    vert = np.lexsort((np.arange(g.n), color)).astype(np.int64)   # rank -> vertex
+    """Rank order (colour asc, splitmix64(id) asc) and the rank-space CSR in the layout of
+    include/gdi.h."""
+    from gdi_synth import splitmix64
+    vert = np.lexsort((splitmix64(np.arange(g.n, dtype=np.uint64)), color)).astype(np.int64)
     rank = np.empty(g.n, dtype=np.int64)
     rank[vert] = np.arange(g.n)
     deg = np.diff(g.row_ptr)
