@@ -145,6 +145,15 @@ int gdi_get_trace(gdi_ctx *ctx, uint64_t *digest, int32_t *G, int64_t *cut);
  * (0 = one wave on every SM).  Results do not depend on any of these (the autotuner relies on it). */
 int gdi_configure(gdi_ctx *ctx, int32_t path, int32_t block, int32_t grid_limit);
 
+/* Autotuner: anneals the first probe_sweeps sweeps of `schedule` (random start, no repair) under
+ * each candidate launch configuration -- threads per block 128/256/512/1024 x one or several
+ * blocks per SM on the CTA path, 100/75/50 % of the SMs on the grid path -- times each with CUDA
+ * events on a private stream, and keeps the fastest for later calls (as gdi_configure would).
+ * Results never depend on the configuration, so tuning is free of side effects on correctness;
+ * it does overwrite the context's spins and results.  Blocking.  Outputs may be NULL. */
+int gdi_autotune(gdi_ctx *ctx, const gdi_schedule *schedule, int32_t probe_sweeps,
+                 int32_t *block_out, int32_t *grid_out, float *ms_out);
+
 /* What the last gdi_anneal launched: path, blocks, dynamic shared memory per block, and how many
  * times the grid-scale path took its exact fallback (0 on the CTA path).  Synchronises. */
 int gdi_last_launch(gdi_ctx *ctx, int32_t *path, int32_t *grid, int64_t *smem_bytes,

@@ -27,7 +27,7 @@ ERRORS = {
 # every entry point that include/gdi.h declares
 EXPORTS = ["gdi_create", "gdi_anneal", "gdi_get_spins", "gdi_get_results", "gdi_cut", "gdi_balance",
            "gdi_get_trace", "gdi_configure", "gdi_last_launch", "gdi_info", "gdi_destroy",
-           "gdi_strerror", "gdi_last_error", "gdi_anneal_static"]
+           "gdi_strerror", "gdi_last_error", "gdi_anneal_static", "gdi_autotune"]
 GDI_PATH_AUTO, GDI_PATH_CTA, GDI_PATH_GRID = 0, 1, 2
 
 
@@ -79,6 +79,7 @@ def load():
     L.gdi_get_trace.argtypes = [vp, vp, vp, vp]
     L.gdi_info.argtypes = [vp, vp, vp, vp]
     L.gdi_configure.argtypes = [vp, i32, i32, i32]
+    L.gdi_autotune.argtypes = [vp, C.POINTER(gdi_schedule), i32, vp, vp, vp]
     L.gdi_anneal_static.argtypes = [i32, vp, vp, i32, vp, i32, i32, i32, i32, i32, i32, vp, vp, vp,
                                     i32, i32, i32, i32, C.c_uint64, i32, vp, vp, vp]
     L.gdi_last_launch.argtypes = [vp, vp, vp, vp, vp]
@@ -219,6 +220,25 @@ class Annealer:
     def configure(self, path: int = GDI_PATH_AUTO, block: int = 0, grid_limit: int = 0):
         _check(load().gdi_configure(self._h, path, block, grid_limit))
         return self
+
+    def autotune(self, schedule: Schedule, probe_sweeps: int = 20):
+        """Time candidate launch configurations on a schedule prefix and keep the fastest."""
+        b = np.zeros(1, np.int32)
+        g = np.zeros(1, np.int32)
+        ms = np.zeros(1, np.float32)
+        s = schedule.c()
+        _check(load().gdi_autotune(self._h, C.byref(s), probe_sweeps, b.ctypes.data, g.ctypes.data, ms.ctypes.data))
+        return dict(block=int(b[0]), grid=int(g[0]), ms=float(ms[0]))
+
+    def capture_graph(self, schedule: Schedule, seed: int, stream, flags: int = 0):
+        """Capture one anneal (random start) into a CUDA graph on `stream` (a torch.cuda.Stream);
+        returns the torch.cuda.CUDAGraph, whose replay() re-runs it.  Call anneal() once with the
+        same schedule before capturing so that every buffer and the table already exist."""
+        import torch
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=stream):
+            self.anneal(schedule, seed, flags=flags, stream=torch.cuda.current_stream())
+        return graph
 
     def last_launch(self):
         pa = np.zeros(1, np.int32)

@@ -87,6 +87,16 @@ struct gdi_ctx {
     DevBuf<uint32_t> tab;
     DevBuf<int32_t> tab_off;
     DevBuf<float> temp;
+    DevBuf<int32_t> item_order, item_counter;
+    // pinned staging of the per-anneal host->device copies, so that an anneal can be captured in
+    // a CUDA graph (no pageable copies, no allocation once the buffers exist)
+    uint32_t *h_tab = nullptr;
+    int32_t *h_off = nullptr;
+    float *h_temp = nullptr;
+    size_t h_tab_n = 0, h_off_n = 0;
+    bool tab_valid = false;
+    gdi_schedule tab_sched{};
+    int32_t tab_ecap = 0, tab_max_row = 0;
     DevBuf<int32_t> raw_G, final_G, tr_G, err;
     DevBuf<int64_t> raw_cut, final_cut, tr_cut;
     DevBuf<uint64_t> tr_digest;
@@ -128,6 +138,11 @@ struct gdi_ctx {
         g_packed.release(); g_rflags.release(); g_tables.release(); g_gin.release(); g_Gcls.release();
         g_err.release(); g_status.release(); g_rhist.release(); g_rties.release(); g_rparams.release();
         g_bar.release();
+        item_order.release(); item_counter.release();
+        if (h_tab) cudaFreeHost(h_tab);
+        if (h_off) cudaFreeHost(h_off);
+        if (h_temp) cudaFreeHost(h_temp);
+        h_tab = nullptr; h_off = nullptr; h_temp = nullptr; h_tab_n = h_off_n = 0;
     }
     GdiGridScratch grid_scratch()
     {
@@ -434,6 +449,19 @@ int gdi_create(gdi_ctx **out, const gdi_graph *g, const gdi_model *m)
     GDI_UP(c->class_off, class_off);
     GDI_UP(c->class_ptr, class_ptr);
     GDI_UP(c->rank_of, rank_of);
+    {
+        // work queue order for the CTA path: largest instance (vertices + CSR entries) first
+        std::vector<int32_t> order((size_t)Q * c->R);
+        for (size_t i = 0; i < order.size(); ++i) order[i] = (int32_t)i;
+        std::vector<int64_t> work((size_t)Q);
+        for (int32_t q = 0; q < Q; ++q)
+            work[(size_t)q] = (inst[(size_t)q + 1] - inst[(size_t)q]) + (g->row_ptr[inst[(size_t)q + 1]] - g->row_ptr[inst[(size_t)q]]);
+        const int32_t Rr = c->R;
+        std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+            return work[(size_t)(a / Rr)] > work[(size_t)(b / Rr)];
+        });
+        GDI_UP(c->item_order, order);
+    }
 #undef GDI_UP
     e = c->spins.alloc((size_t)c->R * (size_t)N);
     if (e == cudaSuccess) e = c->raw_G.alloc((size_t)Q * c->R);
@@ -441,6 +469,7 @@ int gdi_create(gdi_ctx **out, const gdi_graph *g, const gdi_model *m)
     if (e == cudaSuccess) e = c->raw_cut.alloc((size_t)Q * c->R);
     if (e == cudaSuccess) e = c->final_cut.alloc((size_t)Q * c->R);
     if (e == cudaSuccess) e = c->err.alloc(4);
+    if (e == cudaSuccess) e = c->item_counter.alloc(1);
     if (e != cudaSuccess) {
         c->release();
         delete c;
@@ -463,28 +492,62 @@ int gdi_anneal(gdi_ctx *c, const gdi_schedule *S, const gdi_run *run)
     if (!cont && !run->init_spins && s_begin != 0)
         return fail(GDI_ERR_INVALID_ARG, "a random start must begin at sweep 0");
 
-    std::vector<uint32_t> tab;
-    std::vector<int32_t> off;
-    std::vector<float> temp;
+    // the device table is rebuilt only when the schedule changes (then the previous anneal, which
+    // may still read it, is waited for); repeated anneals with one schedule enqueue no copies, so
+    // they can be captured in a CUDA graph
+    cudaStream_t st = (cudaStream_t)run->stream;
+    cudaError_t e = cudaSuccess;
+    const bool same = c->tab_valid && c->tab_sched.mode == S->mode && c->tab_sched.t0 == S->t0 &&
+                      c->tab_sched.t1 == S->t1 && c->tab_sched.pf0 == S->pf0 &&
+                      c->tab_sched.pf1 == S->pf1 && c->tab_sched.sweeps == S->sweeps;
     int32_t ecap = 0, max_row = 0;
-    int rc = build_table(*S, tab, off, temp, ecap, max_row);
-    if (rc) return rc;
+    if (same) {
+        ecap = c->tab_ecap;
+        max_row = c->tab_max_row;
+    } else {
+        std::vector<uint32_t> tab;
+        std::vector<int32_t> off;
+        std::vector<float> temp;
+        int rc = build_table(*S, tab, off, temp, ecap, max_row);
+        if (rc) return rc;
+        if (c->annealed) {
+            e = cudaStreamSynchronize(c->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
+        }
+        e = c->tab.alloc(tab.size());
+        if (e == cudaSuccess) e = c->tab_off.alloc(off.size());
+        if (e == cudaSuccess) e = c->temp.alloc(temp.size());
+        if (e != cudaSuccess) return fail(GDI_ERR_OOM, "device allocation failed (table)");
+        if (c->h_tab_n < tab.size() || c->h_off_n < off.size()) {
+            if (c->h_tab) cudaFreeHost(c->h_tab);
+            if (c->h_off) cudaFreeHost(c->h_off);
+            if (c->h_temp) cudaFreeHost(c->h_temp);
+            c->h_tab = nullptr; c->h_off = nullptr; c->h_temp = nullptr;
+            c->h_tab_n = c->h_off_n = 0;
+            e = cudaMallocHost((void **)&c->h_tab, std::max<size_t>(tab.size(), 1) * sizeof(uint32_t));
+            if (e == cudaSuccess) e = cudaMallocHost((void **)&c->h_off, off.size() * sizeof(int32_t));
+            if (e == cudaSuccess) e = cudaMallocHost((void **)&c->h_temp, off.size() * sizeof(float));
+            if (e != cudaSuccess) return fail(GDI_ERR_OOM, "pinned host allocation failed");
+            c->h_tab_n = std::max<size_t>(tab.size(), 1);
+            c->h_off_n = off.size();
+        }
+        std::memcpy(c->h_tab, tab.data(), tab.size() * sizeof(uint32_t));
+        std::memcpy(c->h_off, off.data(), off.size() * sizeof(int32_t));
+        std::memcpy(c->h_temp, temp.data(), temp.size() * sizeof(float));
+        e = cudaMemcpyAsync(c->tab.p, c->h_tab, tab.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(c->tab_off.p, c->h_off, off.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(c->temp.p, c->h_temp, temp.size() * sizeof(float), cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) { c->tab_valid = false; return cuda_fail(e, "table upload"); }
+        c->tab_valid = true;
+        c->tab_sched = *S;
+        c->tab_ecap = ecap;
+        c->tab_max_row = max_row;
+    }
     // integer ranges: |B h + 4A - E*| and |G| must stay far below the 2^30 threshold sentinels
     if ((int64_t)c->B * c->max_degree + 4LL * c->A + ecap >= ((int64_t)1 << 29))
         return fail(GDI_ERR_OVERFLOW, "B * max_degree + 4A + E_cap must stay below 2^29");
-
-    cudaStream_t st = (cudaStream_t)run->stream;
-    cudaError_t e = c->tab.alloc(tab.size());
-    if (e == cudaSuccess) e = c->tab_off.alloc(off.size());
-    if (e == cudaSuccess) e = c->temp.alloc(temp.size());
-    if (e != cudaSuccess) return fail(GDI_ERR_OOM, "device allocation failed (table)");
-    // pageable source: the copy is staged before cudaMemcpyAsync returns
-    e = cudaMemcpyAsync(c->tab.p, tab.data(), tab.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(c->tab_off.p, off.data(), off.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(c->temp.p, temp.data(), temp.size() * sizeof(float), cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) return cuda_fail(e, "table upload");
 
     const bool trace = (run->flags & GDI_FLAG_TRACE) != 0;
     const size_t items = (size_t)c->Q * c->R;
@@ -538,6 +601,8 @@ int gdi_anneal(gdi_ctx *c, const gdi_schedule *S, const gdi_run *run)
     R.tr_G = trace ? c->tr_G.p : nullptr;
     R.tr_cut = trace ? c->tr_cut.p : nullptr;
     R.err = c->err.p;
+    R.item_order = c->item_order.p;
+    R.item_counter = c->item_counter.p;
 
     size_t need = 0;
     int H = 0;
@@ -549,6 +614,7 @@ int gdi_anneal(gdi_ctx *c, const gdi_schedule *S, const gdi_run *run)
     if (c->path == GDI_PATH_GRID) grid = true;
     else if (c->path == GDI_PATH_AUTO) grid = (c->Q == 1 && (c->max_n > 32768 || need > (size_t)max_optin));
     if (!grid) {
+        cudaMemsetAsync(c->item_counter.p, 0, sizeof(int32_t), st);
         if (need > (size_t)max_optin)
             return fail(GDI_ERR_TOO_LARGE, "instance needs " + std::to_string(need) +
                                                " bytes of shared memory per block (limit " +
@@ -700,6 +766,69 @@ int gdi_configure(gdi_ctx *c, int32_t path, int32_t block, int32_t grid_limit)
     c->path = path;
     if (block) c->block = block;
     c->grid_limit = grid_limit;
+    return GDI_OK;
+}
+
+int gdi_autotune(gdi_ctx *c, const gdi_schedule *S, int32_t probe_sweeps, int32_t *block_out,
+                 int32_t *grid_out, float *ms_out)
+{
+    if (!c || !S) return fail(GDI_ERR_INVALID_ARG, "null argument");
+    if (probe_sweeps < 1 || probe_sweeps > S->sweeps) return fail(GDI_ERR_INVALID_ARG, "probe_sweeps outside the schedule");
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+    cudaStream_t st = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e != cudaSuccess) return cuda_fail(e, "autotune setup");
+    // candidate launch configurations: (block, grid cap); the grid path ignores the block size
+    std::vector<std::pair<int, int>> cand;
+    const bool grid_path = c->path == GDI_PATH_GRID || (c->path == GDI_PATH_AUTO && c->Q == 1 && c->max_n > 32768);
+    if (grid_path) {
+        for (int g : {sms, (sms * 3) / 4, sms / 2}) cand.push_back({c->block, g});
+    } else {
+        for (int b : {128, 256, 512, 1024})
+            for (int g : {0, sms}) cand.push_back({b, g});
+    }
+    const int keep_block = c->block, keep_grid = c->grid_limit;
+    float best = 1e30f;
+    int best_b = keep_block, best_g = keep_grid, rc = GDI_OK;
+    gdi_run run{};
+    run.seed = 0x5eedULL;
+    run.last_sweep = probe_sweeps;
+    run.flags = GDI_FLAG_NO_REPAIR;
+    run.stream = st;
+    for (const auto &cg : cand) {
+        c->block = cg.first;
+        c->grid_limit = cg.second;
+        float ms = 1e30f;
+        for (int rep = 0; rep < 2 && rc == GDI_OK; ++rep) {
+            cudaEventRecord(e0, st);
+            rc = gdi_anneal(c, S, &run);
+            cudaEventRecord(e1, st);
+            if (rc != GDI_OK) break;
+            e = cudaEventSynchronize(e1);
+            if (e != cudaSuccess) { rc = cuda_fail(e, "autotune timing"); break; }
+            float t = 0.f;
+            cudaEventElapsedTime(&t, e0, e1);
+            if (rep == 1) ms = t;
+        }
+        if (rc == GDI_ERR_TOO_LARGE) { rc = GDI_OK; continue; }   // a block size that does not fit
+        if (rc != GDI_OK) break;
+        if (ms < best) { best = ms; best_b = cg.first; best_g = cg.second; }
+    }
+    cudaStreamSynchronize(st);
+    c->stream = nullptr;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamDestroy(st);
+    if (rc != GDI_OK) { c->block = keep_block; c->grid_limit = keep_grid; return rc; }
+    c->block = best_b;
+    c->grid_limit = best_g;
+    if (block_out) *block_out = best_b;
+    if (grid_out) *grid_out = best_g;
+    if (ms_out) *ms_out = best;
     return GDI_OK;
 }
 

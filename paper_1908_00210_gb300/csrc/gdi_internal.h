@@ -58,6 +58,8 @@ struct GdiDevRun {
     int32_t *tr_G;
     int64_t *tr_cut;
     int32_t *err;                    // device error word (0 = ok)
+    const int32_t *item_order;       // [Q*R] items, largest instance first (CTA path)
+    int32_t *item_counter;           // [1] next item to take (zeroed before the launch)
 };
 
 // record a failure for gdi_last_error() (gdi_api.cpp); returns code

@@ -6,6 +6,9 @@
 // block loops over its work items (persistent), sweeps, colour classes and windows without
 // leaving the kernel, so an anneal of M sweeps is one launch.
 //
+// Work items are taken from a size-sorted queue (an atomic counter over the largest-first order),
+// so long instances start first and short ones fill the tail.
+//
 // Per window (a chunk of W consecutive ranks of one colour class):
 //   1. thresholds: for every spin, the local field h_i = sum_j w_ij s_j over its CSR row (Eq. 2),
 //      a Philox4x32-10 draw u_i, the largest energy change E*(u_i) that the draw accepts (binary
@@ -254,7 +257,16 @@ __global__ void __launch_bounds__(BS) gdi_cta_anneal_kernel(GdiDevProblem P, Gdi
         S.flag = reinterpret_cast<int8_t *>(p);
     }
     const int32_t items = P.num_instances * P.replicas;
-    for (int32_t item = blockIdx.x; item < items; item += gridDim.x) {
+    __shared__ int32_t next_item;
+    while (true) {
+        // persistent blocks take (instance, replica) items from a queue sorted by size, largest
+        // first; items are independent, so the assignment does not change any result
+        __syncthreads();
+        if (threadIdx.x == 0) next_item = atomicAdd(R.item_counter, 1);
+        __syncthreads();
+        const int32_t slot = next_item;
+        if (slot >= items) break;
+        const int32_t item = R.item_order[slot];
         const int32_t q = item / P.replicas;
         const int32_t rep = item - q * P.replicas;
         const int64_t base = P.node_off[q];

@@ -1,0 +1,82 @@
+"""Batched launch: many instances in one persistent launch, launch configuration chosen by the
+autotuner without changing any result, and CUDA-graph capture of an anneal."""
+import numpy as np
+import pytest
+
+import oracle
+from gdi_synth import barabasi_albert, batch_union, er_batch
+
+pytestmark = pytest.mark.gpu
+
+
+def _run(gdi, u, inst_ptr, sch, seed, block=0, grid=0, autotune=False):
+    ann = gdi.Annealer(u, A=1, B=4, W=256, replicas=2, inst_ptr=inst_ptr)
+    tuned = None
+    if autotune:
+        tuned = ann.autotune(sch, probe_sweeps=5)
+    elif block or grid:
+        ann.configure(path=gdi.GDI_PATH_CTA, block=block, grid_limit=grid)
+    ann.anneal(sch, seed, flags=gdi.GDI_FLAG_TRACE)
+    out = (ann.trace()[0].copy(), ann.spins().copy(), ann.results()["final_cut"].copy(), ann.last_launch())
+    ann.close()
+    return out, tuned
+
+
+def test_results_do_not_depend_on_launch_configuration(gdi):
+    gs = er_batch(40, 7000, n_lo=150, n_hi=900)
+    inst_ptr, u = batch_union(gs)
+    sch = gdi.Schedule(sweeps=60, t0=12.0, t1=0.2)
+    ref, _ = _run(gdi, u, inst_ptr, sch, 17)
+    for block, grid in [(128, 0), (1024, 0), (256, 7), (512, 152)]:
+        got, _ = _run(gdi, u, inst_ptr, sch, 17, block=block, grid=grid)
+        assert np.array_equal(got[0], ref[0]), (block, grid)
+        assert np.array_equal(got[1], ref[1]), (block, grid)
+        assert got[3]["grid"] <= (grid or 10 ** 9)
+    got, tuned = _run(gdi, u, inst_ptr, sch, 17, autotune=True)
+    assert tuned["block"] in (128, 256, 512, 1024) and tuned["ms"] > 0
+    assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1])
+    # and the oracle agrees on a few instances
+    for q in (0, 13, 39):
+        r = oracle.anneal(gs[q], A=1, B=4, W=256, t0=12.0, t1=0.2, sweeps=60, seed=17, instance=q,
+                          replicas=2)
+        assert np.array_equal(ref[2][q], r.final_cut)
+        assert np.array_equal(ref[1][:, inst_ptr[q]:inst_ptr[q + 1]], r.spins)
+
+
+def test_grid_path_autotune_keeps_results(gdi):
+    g = barabasi_albert(40000, 5, 71)
+    sch = gdi.Schedule(sweeps=20, t0=12.0, t1=0.2)
+    a = gdi.Annealer(g, A=1, B=4, W=128, replicas=8)
+    a.configure(path=gdi.GDI_PATH_GRID)
+    a.anneal(sch, 3, flags=gdi.GDI_FLAG_TRACE)
+    d0, s0 = a.trace()[0].copy(), a.spins().copy()
+    tuned = a.autotune(sch, probe_sweeps=4)
+    a.anneal(sch, 3, flags=gdi.GDI_FLAG_TRACE)
+    assert np.array_equal(a.trace()[0], d0) and np.array_equal(a.spins(), s0)
+    assert tuned["grid"] > 0
+    a.close()
+
+
+@pytest.mark.parametrize("grid_path", [False, True])
+def test_cuda_graph_replay_equals_direct_anneal(gdi, grid_path):
+    import torch
+    if grid_path:
+        g = barabasi_albert(40000, 5, 72)
+        a = gdi.Annealer(g, A=1, B=4, W=128, replicas=8)
+        a.configure(path=gdi.GDI_PATH_GRID)
+    else:
+        gs = er_batch(30, 8000, n_lo=200, n_hi=600)
+        inst_ptr, g = batch_union(gs)
+        a = gdi.Annealer(g, A=1, B=4, W=64, replicas=3, inst_ptr=inst_ptr)
+    sch = gdi.Schedule(sweeps=40, t0=12.0, t1=0.2)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        a.anneal(sch, 21, stream=stream)
+    ref_spins, ref_cut = a.spins().copy(), a.results()["final_cut"].copy()
+    graph = a.capture_graph(sch, 21, stream)
+    for _ in range(2):
+        graph.replay()
+        torch.cuda.synchronize()
+        assert np.array_equal(a.spins(), ref_spins)
+        assert np.array_equal(a.results()["final_cut"], ref_cut)
+    a.close()
