@@ -9,8 +9,8 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 LIB = os.path.join(PKG, "libgdi.so")
-SOURCES = ["gdi_kernels.cu", "gdi_grid.cu", "gdi_static.cu", "gdi_api.cpp"]
-HEADERS = ["gdi_internal.h", "gdi_device.cuh", os.path.join(ROOT, "include", "gdi.h")]
+SOURCES = ["gdi_kernels.cu", "gdi_grid.cu", "gdi_static.cu", "gdi_mpnn.cu", "gdi_api.cpp"]
+HEADERS = ["gdi_internal.h", "gdi_device.cuh", os.path.join(ROOT, "include", "gdi.h"), os.path.join(ROOT, "include", "gdi_mpnn.h")]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 

@@ -1,0 +1,386 @@
+"""Learned warm start: a message-passing network that predicts where annealing should start.
+
+Every computation runs in libgdi.so's kernels (include/gdi_mpnn.h); this module only holds device
+buffers (torch tensors) and calls the C ABI.  The plain random-start annealer produces the training
+labels and judges the result: a graph is "reached" when an anneal from the network's exactly
+balanced prediction, started at a low temperature, matches the median cut of full random-start
+anneals.
+
+    python -m paper_1908_00210_gb300.learn --train 1024 --test 128 --out results.json
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes as C
+import json
+import math
+import os
+import time
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _binding as B
+
+HID = 64
+FIN = 16
+LAYER_DIMS = [(FIN, HID), (HID, HID), (HID, HID)]
+
+MPNN_EXPORTS = ["gdi_mpnn_features", "gdi_mpnn_aggregate", "gdi_mpnn_dense_fwd", "gdi_mpnn_dense_bwd",
+                "gdi_mpnn_wgrad", "gdi_mpnn_out_fwd", "gdi_mpnn_out_bwd", "gdi_mpnn_loss",
+                "gdi_mpnn_adam", "gdi_mpnn_to_bf16", "gdi_mpnn_round"]
+
+_L = None
+
+
+def lib():
+    global _L
+    if _L is None:
+        L = B.load()
+        vp, i32, i64, f32, u64 = C.c_void_p, C.c_int32, C.c_int64, C.c_float, C.c_uint64
+        L.gdi_mpnn_features.argtypes = [i64, i32, vp, vp, vp, vp, u64, i32, vp, vp, vp]
+        L.gdi_mpnn_aggregate.argtypes = [i64, vp, vp, vp, i32, vp, i32, i32, vp]
+        L.gdi_mpnn_dense_fwd.argtypes = [i64, vp, vp, i32, vp, vp, vp, vp, vp]
+        L.gdi_mpnn_dense_bwd.argtypes = [i64, i32, vp, vp, vp, vp, vp, vp, vp, vp]
+        L.gdi_mpnn_wgrad.argtypes = [i64, vp, i32, vp, i32, vp, vp, vp]
+        L.gdi_mpnn_out_fwd.argtypes = [i64, vp, vp, vp, vp, vp]
+        L.gdi_mpnn_out_bwd.argtypes = [i64, vp, vp, vp, vp]
+        L.gdi_mpnn_loss.argtypes = [i32, vp, vp, vp, f32, vp, vp, vp, vp]
+        L.gdi_mpnn_adam.argtypes = [i64, vp, vp, vp, vp, vp, f32, f32, f32, f32, i32, vp]
+        L.gdi_mpnn_to_bf16.argtypes = [i64, vp, vp, vp]
+        L.gdi_mpnn_round.argtypes = [i32, vp, i32, vp, vp, vp]
+        for n in MPNN_EXPORTS:
+            getattr(L, n).restype = C.c_int
+        _L = L
+    return _L
+
+
+def _ok(rc, what):
+    if rc != 0:
+        raise B.GdiError(rc, what)
+
+
+def param_layout():
+    off, o = {}, 0
+    for l, (din, dout) in enumerate(LAYER_DIMS, start=1):
+        off[f"Ws{l}"] = (o, din * dout); o += din * dout
+        off[f"Wn{l}"] = (o, din * dout); o += din * dout
+        off[f"b{l}"] = (o, dout); o += dout
+    off["wo"] = (o, HID); o += HID
+    off["bo"] = (o, 1); o += 1
+    return off, o
+
+
+def init_params(seed: int = 0) -> np.ndarray:
+    """Glorot-uniform matrices, zero biases (float32 master weights)."""
+    off, total = param_layout()
+    rng = np.random.default_rng(seed)
+    p = np.zeros(total, dtype=np.float32)
+    for l, (din, dout) in enumerate(LAYER_DIMS, start=1):
+        a = math.sqrt(6.0 / (din + dout))
+        for k in ("Ws", "Wn"):
+            o, n = off[f"{k}{l}"]
+            p[o:o + n] = rng.uniform(-a, a, n)
+    o, n = off["wo"]
+    p[o:o + n] = rng.uniform(-math.sqrt(6 / (HID + 1)), math.sqrt(6 / (HID + 1)), n)
+    return p
+
+
+@dataclass
+class GraphBatch:
+    """A disjoint union of graphs resident on the device."""
+    N: int
+    G: int
+    max_n: int
+    graph_ptr_h: np.ndarray
+    row_ptr: "object"
+    col: "object"
+    graph_ptr: "object"
+    graph_id: "object"
+    graphs: list
+
+    @staticmethod
+    def from_graphs(graphs, graph_ids=None, device="cuda"):
+        import torch
+        from gdi_synth import batch_union
+        gp, u = batch_union(graphs)
+        ids = np.arange(len(graphs), dtype=np.uint32) if graph_ids is None else np.asarray(graph_ids, dtype=np.uint32)
+        return GraphBatch(N=int(u.n), G=len(graphs), max_n=int(max(g.n for g in graphs)), graph_ptr_h=gp,
+                          row_ptr=torch.from_numpy(u.row_ptr).to(device),
+                          col=torch.from_numpy(u.col).to(device),
+                          graph_ptr=torch.from_numpy(gp).to(device),
+                          graph_id=torch.from_numpy(ids.view(np.int32)).to(device), graphs=list(graphs))
+
+
+class MPNN:
+    """Parameters, optimiser state and activation buffers of the network on the device."""
+
+    def __init__(self, params: np.ndarray | None = None, seed: int = 0, lr: float = 1e-3,
+                 lam: float = 0.1, feat_seed: int = 0x9E3779B9, steps: int = 4):
+        import torch
+        self.torch = torch
+        off, total = param_layout()
+        self.off, self.P = off, total
+        p = init_params(seed) if params is None else np.asarray(params, dtype=np.float32)
+        self.params = torch.from_numpy(p.copy()).cuda()
+        self.params_bf16 = torch.zeros(total, dtype=torch.int16, device="cuda")
+        self.grads = torch.zeros(total, dtype=torch.float32, device="cuda")
+        self.m = torch.zeros_like(self.grads)
+        self.v = torch.zeros_like(self.grads)
+        self.step = 0
+        self.lr, self.lam, self.feat_seed, self.steps = lr, lam, feat_seed, steps
+        _ok(lib().gdi_mpnn_to_bf16(total, self.params.data_ptr(), self.params_bf16.data_ptr(), self._st()), "to_bf16")
+
+    def _st(self):
+        return C.c_void_p(self.torch.cuda.current_stream().cuda_stream)
+
+    def _pf(self, key):      # float32 master slice
+        return self.params.data_ptr() + 4 * self.off[key][0]
+
+    def _pb(self, key):      # bf16 slice
+        return self.params_bf16.data_ptr() + 2 * self.off[key][0]
+
+    def _gf(self, key):
+        return self.grads.data_ptr() + 4 * self.off[key][0]
+
+    # ---------------------------------------------------------------- forward / backward -----
+    def features(self, b: GraphBatch):
+        t = self.torch
+        X = t.empty((b.N, FIN), dtype=t.float32, device="cuda")
+        scratch = t.empty((2 * b.N * 8,), dtype=t.float32, device="cuda")
+        _ok(lib().gdi_mpnn_features(b.N, b.G, b.graph_ptr.data_ptr(), b.graph_id.data_ptr(), b.row_ptr.data_ptr(),
+                                    b.col.data_ptr(), self.feat_seed, self.steps, X.data_ptr(), scratch.data_ptr(),
+                                    self._st()), "features")
+        return X
+
+    def forward(self, b: GraphBatch, X=None):
+        t = self.torch
+        L = lib()
+        if X is None:
+            X = self.features(b)
+        cache = []
+        h = X
+        for l, (din, dout) in enumerate(LAYER_DIMS, start=1):
+            agg = t.empty((b.N, din), dtype=t.float32, device="cuda")
+            _ok(L.gdi_mpnn_aggregate(b.N, b.row_ptr.data_ptr(), b.col.data_ptr(), h.data_ptr(), din, agg.data_ptr(),
+                                     0, 0, self._st()), "aggregate")
+            out = t.empty((b.N, HID), dtype=t.float32, device="cuda")
+            _ok(L.gdi_mpnn_dense_fwd(b.N, h.data_ptr(), agg.data_ptr(), din, self._pb(f"Ws{l}"), self._pb(f"Wn{l}"),
+                                     self._pf(f"b{l}"), out.data_ptr(), self._st()), "dense_fwd")
+            cache.append((h, agg, out, din))
+            h = out
+        z = t.empty((b.N,), dtype=t.float32, device="cuda")
+        _ok(L.gdi_mpnn_out_fwd(b.N, h.data_ptr(), self._pb("wo"), self._pf("bo"), z.data_ptr(), self._st()), "out_fwd")
+        return z, cache
+
+    def loss_and_backward(self, b: GraphBatch, y, z, cache):
+        """Loss (device scalar) and the gradients in self.grads."""
+        t = self.torch
+        L = lib()
+        self.grads.zero_()
+        loss = t.zeros(1, dtype=t.float32, device="cuda")
+        stats = t.empty((b.G, 4), dtype=t.float32, device="cuda")
+        dz = t.empty((b.N,), dtype=t.float32, device="cuda")
+        _ok(L.gdi_mpnn_loss(b.G, b.graph_ptr.data_ptr(), z.data_ptr(), y.data_ptr(), self.lam, stats.data_ptr(),
+                            dz.data_ptr(), loss.data_ptr(), self._st()), "loss")
+        h3 = cache[-1][2]
+        _ok(L.gdi_mpnn_wgrad(b.N, h3.data_ptr(), HID, dz.data_ptr(), 1, self._gf("wo"), self._gf("bo"), self._st()),
+            "wgrad out")
+        dh = t.empty((b.N, HID), dtype=t.float32, device="cuda")
+        _ok(L.gdi_mpnn_out_bwd(b.N, self._pb("wo"), dz.data_ptr(), dh.data_ptr(), self._st()), "out_bwd")
+        for l in (3, 2, 1):
+            h_in, agg, out, din = cache[l - 1]
+            dpre = t.empty((b.N, HID), dtype=t.float32, device="cuda")
+            dxs = t.empty((b.N, din), dtype=t.float32, device="cuda")
+            tt = t.empty((b.N, din), dtype=t.float32, device="cuda")
+            _ok(L.gdi_mpnn_dense_bwd(b.N, din, self._pb(f"Ws{l}"), self._pb(f"Wn{l}"), out.data_ptr(), dh.data_ptr(),
+                                     dpre.data_ptr(), dxs.data_ptr(), tt.data_ptr(), self._st()), "dense_bwd")
+            _ok(L.gdi_mpnn_wgrad(b.N, h_in.data_ptr(), din, dpre.data_ptr(), HID, self._gf(f"Ws{l}"), self._gf(f"b{l}"),
+                                 self._st()), "wgrad Ws")
+            _ok(L.gdi_mpnn_wgrad(b.N, agg.data_ptr(), din, dpre.data_ptr(), HID, self._gf(f"Wn{l}"), None, self._st()),
+                "wgrad Wn")
+            if l > 1:
+                _ok(L.gdi_mpnn_aggregate(b.N, b.row_ptr.data_ptr(), b.col.data_ptr(), tt.data_ptr(), din, dxs.data_ptr(),
+                                         1, 1, self._st()), "aggregate T")
+                dh = dxs
+        return loss, stats
+
+    def adam(self, beta1=0.9, beta2=0.999, eps=1e-8):
+        self.step += 1
+        _ok(lib().gdi_mpnn_adam(self.P, self.params.data_ptr(), self.grads.data_ptr(), self.m.data_ptr(),
+                                self.v.data_ptr(), self.params_bf16.data_ptr(), self.lr, beta1, beta2, eps, self.step,
+                                self._st()), "adam")
+
+    def train_step(self, b: GraphBatch, y):
+        z, cache = self.forward(b)
+        loss, _ = self.loss_and_backward(b, y, z, cache)
+        self.adam()
+        return loss
+
+    def predict_spins(self, b: GraphBatch):
+        """Exactly balanced spins (int8, device [N]) from the network's logits."""
+        t = self.torch
+        z, _ = self.forward(b)
+        s = t.empty((b.N,), dtype=t.int8, device="cuda")
+        _ok(lib().gdi_mpnn_round(b.G, b.graph_ptr.data_ptr(), b.max_n, z.data_ptr(), s.data_ptr(), self._st()), "round")
+        return s
+
+
+# -------------------------------------------------------------------- data and evaluation -----
+def make_graphs(count: int, seed0: int, n_lo=1000, n_hi=5000):
+    """Half Erdos-Renyi (mean degree ~ U[3, 48]), half random geometric (mean degree ~ U[4, 32])."""
+    from gdi_synth import erdos_renyi, random_geometric, uniform01
+    out = []
+    for i in range(count):
+        s = seed0 + i
+        u = uniform01(s, 11, np.arange(3))
+        n = int(n_lo + u[0] * (n_hi - n_lo + 1))
+        if i % 2 == 0:
+            d = 3.0 + 45.0 * u[1]
+            out.append(erdos_renyi(n, d / (n - 1), s, name=f"er{s}"))
+        else:
+            d = 4.0 + 28.0 * u[1]
+            r = math.sqrt(d / (math.pi * (n - 1)))
+            out.append(random_geometric(n, r, s, name=f"rgg{s}"))
+    return out
+
+
+def anneal_batch(graphs, *, sweeps, t0, t1, seed, replicas, init=None, A=1, Bc=4, W=256, stream=None):
+    """Random-start (or given-start) anneal of every graph; returns (final_cut [G, R], spins [R, N],
+    GPU milliseconds of the anneal kernel launch sequence)."""
+    import torch
+    from gdi_synth import batch_union
+    gp, u = batch_union(graphs)
+    ann = B.Annealer(u, A=A, B=Bc, W=W, replicas=replicas, inst_ptr=gp)
+    sch = B.Schedule(sweeps=sweeps, t0=t0 * Bc, t1=t1 * Bc)
+    st = stream or torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    if init is None:
+        ann.anneal(sch, seed, stream=st)
+    else:
+        ann.anneal(sch, seed, init_device_ptr=init.data_ptr(), stream=st)
+    e1.record(st)
+    cut = ann.results()["final_cut"]
+    ms = e0.elapsed_time(e1)
+    spins = ann.spins()
+    ann.close()
+    return cut, spins, ms
+
+
+def label_graphs(graphs, *, sweeps=2000, replicas=4, seed=1):
+    """Labels = the best (lowest repaired cut) of `replicas` plain random-start anneals."""
+    cut, spins, _ = anneal_batch(graphs, sweeps=sweeps, t0=3.0, t1=0.05, seed=seed, replicas=replicas)
+    from gdi_synth import batch_union
+    gp, _ = batch_union(graphs)
+    y = np.empty(gp[-1], dtype=np.int8)
+    for g in range(len(graphs)):
+        best = int(np.argmin(cut[g]))
+        y[gp[g]:gp[g + 1]] = spins[best, gp[g]:gp[g + 1]]
+    return y, cut.min(axis=1)
+
+
+def train(model: MPNN, graphs, labels, *, epochs=30, batch=16, seed=0, log=None):
+    import torch
+    from gdi_synth import batch_union
+    rng = np.random.default_rng(seed)
+    gp_all, _ = batch_union(graphs)
+    history = []
+    batches = []
+    order = np.arange(len(graphs))
+    for ep in range(epochs):
+        rng.shuffle(order)
+        tot = 0.0
+        for k in range(0, len(order), batch):
+            idx = order[k:k + batch]
+            gb = GraphBatch.from_graphs([graphs[i] for i in idx], graph_ids=idx)
+            y = np.concatenate([labels[gp_all[i]:gp_all[i + 1]] for i in idx])
+            loss = model.train_step(gb, torch.from_numpy(y).cuda())
+            tot += float(loss.item()) * len(idx)
+        history.append(tot / len(graphs))
+        if log:
+            log(f"epoch {ep}: loss {history[-1]:.4f}")
+    return history
+
+
+LADDER = [25, 50, 100, 200, 400, 800, 1600, 2000]
+
+
+def evaluate(model: MPNN, graphs, *, seeds=8, full_sweeps=2000, ladder=LADDER, t_low=0.5, log=None):
+    """Time to reach the random-start median cut: learned start at T0 = t_low, random start at
+    T0 = 3.0, random start at T0 = t_low (control), all ending at T = 0.05."""
+    import torch
+    ref_cut, _, full_ms = anneal_batch(graphs, sweeps=full_sweeps, t0=3.0, t1=0.05, seed=101, replicas=seeds)
+    c_ref = np.median(ref_cut, axis=1)
+    gb = GraphBatch.from_graphs(graphs, graph_ids=np.arange(len(graphs)) + 1_000_000)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    pred = model.predict_spins(gb)
+    e1.record()
+    torch.cuda.synchronize()
+    infer_ms = e0.elapsed_time(e1)
+    init = pred.repeat(seeds)            # [seeds * N]: every replica starts from the prediction
+    ns = np.array([g.n for g in graphs], dtype=np.float64)
+    share = ns / ns.sum()                # a graph's share of a batched launch's GPU time
+    methods = {"learned_T0.5": dict(t0=t_low, init=init), "random_T3.0": dict(t0=3.0, init=None),
+               "random_T0.5": dict(t0=t_low, init=None)}
+    out = {"c_ref_median": float(np.median(c_ref)), "full_random_ms": full_ms, "infer_ms": infer_ms,
+           "graphs": len(graphs), "seeds": seeds, "ladder": ladder}
+    for name, m in methods.items():
+        reached_at = np.full(len(graphs), -1)
+        rung_ms = {}
+        for M in ladder:
+            cut, _, ms = anneal_batch(graphs, sweeps=M, t0=m["t0"], t1=0.05, seed=202, replicas=seeds, init=m["init"])
+            rung_ms[M] = ms
+            med = np.median(cut, axis=1)
+            newly = (reached_at < 0) & (med <= c_ref)
+            reached_at[newly] = M
+            if log:
+                log(f"{name} M={M}: reached {int((reached_at > 0).sum())}/{len(graphs)} ({ms:.1f} ms)")
+        t = np.array([rung_ms[M] * share[g] if M > 0 else np.nan for g, M in enumerate(reached_at)])
+        if name.startswith("learned"):
+            t = t + infer_ms * share
+        ok = reached_at > 0
+        out[name] = {"fraction_reached": float(ok.mean()),
+                     "median_sweeps_to_cut": float(np.median(reached_at[ok])) if ok.any() else None,
+                     "median_gpu_ms_to_cut": float(np.median(t[ok])) if ok.any() else None,
+                     "total_gpu_ms_reached_graphs": float(np.nansum(t[ok])), "rung_ms": rung_ms}
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__)
+    ap.add_argument("--train", type=int, default=1024)
+    ap.add_argument("--test", type=int, default=128)
+    ap.add_argument("--epochs", type=int, default=30)
+    ap.add_argument("--label-sweeps", type=int, default=2000)
+    ap.add_argument("--out", default="")
+    args = ap.parse_args()
+    import torch
+    torch.cuda.set_device(0)
+    log = lambda s: print(s, flush=True)  # noqa: E731
+    t0 = time.time()
+    train_graphs = make_graphs(args.train, 500_000)
+    test_graphs = make_graphs(args.test, 900_000)
+    log(f"graphs generated in {time.time() - t0:.1f} s")
+    t0 = time.time()
+    labels, best = label_graphs(train_graphs, sweeps=args.label_sweeps)
+    log(f"labels in {time.time() - t0:.1f} s")
+    model = MPNN(seed=0)
+    t0 = time.time()
+    hist = train(model, train_graphs, labels, epochs=args.epochs, log=log)
+    log(f"trained in {time.time() - t0:.1f} s")
+    res = evaluate(model, test_graphs, log=log)
+    res["train_loss"] = hist
+    res["train_graphs"] = args.train
+    res["label_sweeps"] = args.label_sweeps
+    print(json.dumps({k: v for k, v in res.items() if k != "train_loss"}, default=str))
+    if args.out:
+        with open(args.out, "w") as f:
+            json.dump(res, f, default=str, indent=1)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,111 @@
+"""GPU kernels of the learned warm start against the FP64 network oracle."""
+import numpy as np
+import pytest
+
+from oracle import mpnn as ref
+from gdi_synth import batch_union, erdos_renyi, random_geometric
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def setup(gdi):
+    import torch
+    from paper_1908_00210_gb300 import learn
+    gs = [erdos_renyi(300, 0.03, 11), random_geometric(260, 0.12, 12), erdos_renyi(411, 0.015, 13, signed=False)]
+    ids = np.array([5, 6, 7], dtype=np.uint32)
+    b = learn.GraphBatch.from_graphs(gs, graph_ids=ids)
+    gp, u = batch_union(gs)
+    rng = np.random.default_rng(2)
+    y = np.empty(gp[-1], dtype=np.int8)
+    for g in range(len(gs)):
+        n = gp[g + 1] - gp[g]
+        y[gp[g]:gp[g + 1]] = rng.permutation(np.where(np.arange(n) < n // 2, 1, -1))
+    model = learn.MPNN(seed=3, lam=0.2, feat_seed=12345, steps=3)
+    return learn, torch, gs, ids, b, gp, u, y, model
+
+
+def test_features_match_oracle(setup):
+    learn, torch, gs, ids, b, gp, u, y, model = setup
+    X = model.features(b).cpu().numpy()
+    Xr = ref.features(gp, ids, u.row_ptr, u.col, 12345, 3)
+    assert np.max(np.abs(X - Xr)) < 1e-4
+
+
+def test_forward_logits_within_1e2_of_fp64(setup):
+    learn, torch, gs, ids, b, gp, u, y, model = setup
+    Xr = ref.features(gp, ids, u.row_ptr, u.col, 12345, 3)
+    X = torch.from_numpy(Xr.astype(np.float32)).cuda()
+    z, _ = model.forward(b, X)
+    P = ref.effective_params(model.params.cpu().numpy())
+    zr, _ = ref.forward(P, u.row_ptr, u.col, Xr.astype(np.float32).astype(np.float64))
+    err = np.max(np.abs(z.cpu().numpy() - zr))
+    assert err < 1e-2, err
+    assert err < 1e-3 * max(1.0, np.max(np.abs(zr)))   # float32 activations: far inside the bar
+
+
+def test_gradients_match_oracle_backward(setup):
+    learn, torch, gs, ids, b, gp, u, y, model = setup
+    Xr = ref.features(gp, ids, u.row_ptr, u.col, 12345, 3).astype(np.float32)
+    X = torch.from_numpy(Xr).cuda()
+    z, cache = model.forward(b, X)
+    loss, stats = model.loss_and_backward(b, torch.from_numpy(y).cuda(), z, cache)
+    g = model.grads.cpu().numpy()
+    P = ref.effective_params(model.params.cpu().numpy())
+    zr, cr = ref.forward(P, u.row_ptr, u.col, Xr.astype(np.float64))
+    Lr, dzr, _ = ref.loss(gp, zr, y, model.lam)
+    gr = ref.flat_grads(ref.backward(P, u.row_ptr, u.col, cr, dzr))
+    assert abs(float(loss.item()) - Lr) < 1e-4 * max(1.0, abs(Lr))
+    scale = np.max(np.abs(gr))
+    assert np.max(np.abs(g - gr)) < 2e-3 * scale, (np.max(np.abs(g - gr)), scale)
+
+
+def test_adam_step_matches_oracle(setup):
+    learn, torch, gs, ids, b, gp, u, y, model = setup
+    m2 = learn.MPNN(seed=9, lr=1e-2)
+    rng = np.random.default_rng(1)
+    grad = rng.standard_normal(m2.P).astype(np.float32)
+    p0 = m2.params.cpu().numpy().astype(np.float64)
+    m2.grads.copy_(torch.from_numpy(grad))
+    m2.adam()
+    p1, mm, vv = ref.adam_step(p0, grad.astype(np.float64), np.zeros(m2.P), np.zeros(m2.P), 1e-2, 0.9, 0.999, 1e-8, 1)
+    assert np.max(np.abs(m2.params.cpu().numpy() - p1)) < 1e-6
+    bf = m2.params_bf16.cpu().numpy().view(np.uint16)
+    assert np.array_equal(bf.astype(np.uint32) << 16,
+                          ref.bf16_round(m2.params.cpu().numpy()).astype(np.float32).view(np.uint32))
+
+
+def test_rounding_matches_oracle(gdi):
+    import torch
+    from paper_1908_00210_gb300 import learn
+    rng = np.random.default_rng(7)
+    sizes = [1, 2, 7, 300, 1001, 5000]
+    gp = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    z = (rng.standard_normal(gp[-1]) + 0.1).astype(np.float32)
+    z[10:20] = z[10]                                     # ties inside a graph
+    s = torch.empty(gp[-1], dtype=torch.int8, device="cuda")
+    d_gp = torch.from_numpy(gp).cuda()      # keep the device buffers alive until the kernel ran
+    d_z = torch.from_numpy(z).cuda()
+    rc = learn.lib().gdi_mpnn_round(len(sizes), d_gp.data_ptr(), max(sizes), d_z.data_ptr(), s.data_ptr(), None)
+    assert rc == 0
+    torch.cuda.synchronize()
+    assert np.array_equal(s.cpu().numpy(), ref.round_balanced(gp, z))
+
+
+def test_training_reduces_loss_and_prediction_anneals(setup, gdi):
+    """A few Adam steps on annealer labels reduce the loss; the rounded prediction is exactly
+    balanced and gdi_anneal accepts it as a device-side initial state."""
+    learn, torch, gs, ids, b, gp, u, y, model = setup
+    labels, best = learn.label_graphs(gs, sweeps=300, replicas=2, seed=3)
+    yl = torch.from_numpy(labels).cuda()
+    m = learn.MPNN(seed=4, lr=3e-3, lam=0.1)
+    first = float(m.train_step(b, yl).item())
+    for _ in range(60):
+        last = float(m.train_step(b, yl).item())
+    assert last < first
+    s = m.predict_spins(b)
+    sh = s.cpu().numpy()
+    for g in range(len(gs)):
+        assert abs(int(sh[gp[g]:gp[g + 1]].astype(np.int64).sum())) == (gp[g + 1] - gp[g]) % 2
+    cut, spins, ms = learn.anneal_batch(gs, sweeps=50, t0=0.5, t1=0.05, seed=5, replicas=1, init=s)
+    assert np.all(np.isfinite(cut)) and ms > 0
