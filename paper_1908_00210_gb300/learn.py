@@ -116,7 +116,7 @@ class MPNN:
     """Parameters, optimiser state and activation buffers of the network on the device."""
 
     def __init__(self, params: np.ndarray | None = None, seed: int = 0, lr: float = 1e-3,
-                 lam: float = 0.1, feat_seed: int = 0x9E3779B9, steps: int = 4):
+                 lam: float = 0.1, feat_seed: int = 0x9E3779B9, steps: int = 256):
         import torch
         self.torch = torch
         off, total = param_layout()
@@ -324,10 +324,11 @@ def evaluate(model: MPNN, graphs, *, seeds=8, full_sweeps=2000, ladder=LADDER, t
     init = pred.repeat(seeds)            # [seeds * N]: every replica starts from the prediction
     ns = np.array([g.n for g in graphs], dtype=np.float64)
     share = ns / ns.sum()                # a graph's share of a batched launch's GPU time
-    methods = {"learned_T0.5": dict(t0=t_low, init=init), "random_T3.0": dict(t0=3.0, init=None),
-               "random_T0.5": dict(t0=t_low, init=None)}
+    methods = {f"learned_T{t_low}": dict(t0=t_low, init=init), "random_T3.0": dict(t0=3.0, init=None),
+               f"random_T{t_low}": dict(t0=t_low, init=None)}
     out = {"c_ref_median": float(np.median(c_ref)), "full_random_ms": full_ms, "infer_ms": infer_ms,
            "graphs": len(graphs), "seeds": seeds, "ladder": ladder}
+    times = {}
     for name, m in methods.items():
         reached_at = np.full(len(graphs), -1)
         rung_ms = {}
@@ -343,10 +344,17 @@ def evaluate(model: MPNN, graphs, *, seeds=8, full_sweeps=2000, ladder=LADDER, t
         if name.startswith("learned"):
             t = t + infer_ms * share
         ok = reached_at > 0
+        times[name] = np.where(ok, t, np.nan)
         out[name] = {"fraction_reached": float(ok.mean()),
                      "median_sweeps_to_cut": float(np.median(reached_at[ok])) if ok.any() else None,
                      "median_gpu_ms_to_cut": float(np.median(t[ok])) if ok.any() else None,
                      "total_gpu_ms_reached_graphs": float(np.nansum(t[ok])), "rung_ms": rung_ms}
+    # paired comparison on the graphs that both the learned and the random start reach
+    a, b = times[f"learned_T{t_low}"], times["random_T3.0"]
+    both = np.isfinite(a) & np.isfinite(b)
+    out["paired"] = {"graphs_both_reached": int(both.sum()),
+                     "median_time_ratio_random_over_learned": float(np.median(b[both] / a[both])) if both.any() else None,
+                     "learned_faster_fraction": float(np.mean(a[both] < b[both])) if both.any() else None}
     return out
 
 
@@ -354,8 +362,12 @@ def main():
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--train", type=int, default=1024)
     ap.add_argument("--test", type=int, default=128)
-    ap.add_argument("--epochs", type=int, default=30)
+    ap.add_argument("--epochs", type=int, default=60)
     ap.add_argument("--label-sweeps", type=int, default=2000)
+    ap.add_argument("--steps", type=int, default=256, help="lazy-walk diffusion steps of the features")
+    ap.add_argument("--lr", type=float, default=2e-3)
+    ap.add_argument("--lam", type=float, default=0.1)
+    ap.add_argument("--t-low", type=float, default=0.5)
     ap.add_argument("--out", default="")
     args = ap.parse_args()
     import torch
@@ -368,12 +380,13 @@ def main():
     t0 = time.time()
     labels, best = label_graphs(train_graphs, sweeps=args.label_sweeps)
     log(f"labels in {time.time() - t0:.1f} s")
-    model = MPNN(seed=0)
+    model = MPNN(seed=0, lr=args.lr, lam=args.lam, steps=args.steps)
     t0 = time.time()
     hist = train(model, train_graphs, labels, epochs=args.epochs, log=log)
     log(f"trained in {time.time() - t0:.1f} s")
-    res = evaluate(model, test_graphs, log=log)
+    res = evaluate(model, test_graphs, log=log, t_low=args.t_low)
     res["train_loss"] = hist
+    res["steps"] = args.steps
     res["train_graphs"] = args.train
     res["label_sweeps"] = args.label_sweeps
     print(json.dumps({k: v for k, v in res.items() if k != "train_loss"}, default=str))
