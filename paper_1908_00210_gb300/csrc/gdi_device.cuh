@@ -85,6 +85,19 @@ __device__ __forceinline__ int32_t gamma_of(int sg, int32_t h, int32_t es, int32
     return floor_div_pos(es + B * h - 4 * A, 4 * A);
 }
 
+// gamma_of when 4A = 2^sh: floor division by a power of two is an arithmetic shift
+__device__ __forceinline__ int32_t gamma_of_shift(int sg, int32_t h, int32_t es, int32_t A, int32_t B, int sh)
+{
+    if (sg > 0) {
+        if (es == ES_NONE) return GAM_INF;
+        if (es == ES_ALL) return -GAM_INF;
+        return -((-(B * h + 4 * A - es)) >> sh);          // ceil((B h + 4A - E*) / 4A)
+    }
+    if (es == ES_NONE) return -GAM_INF;
+    if (es == ES_ALL) return GAM_INF;
+    return (es + B * h - 4 * A) >> sh;                    // floor((E* + B h - 4A) / 4A)
+}
+
 // ---------------------------------------------------------------------------------------------
 // block primitives (BS threads, red: shared scratch of >= BS/32 + 1 words of T)
 template <int BS, typename T>

@@ -125,16 +125,27 @@ __device__ bool grid_sync(const GdiGridScratch &X)
 }
 
 // local fields of one rank for all 8 replicas (thread-serial over the row, four neighbours in
-// flight at a time)
-__device__ void field8_thread(const GdiDevProblem &P, int64_t base, int32_t r, const uint8_t *packed,
-                              int32_t h[8])
+// flight at a time), written to hout[0..7] (all replicas) or hout[0] (replica `one` only)
+__device__ __forceinline__ void field8_thread(const GdiDevProblem &P, int64_t base, int32_t r,
+                                              const uint8_t *packed, int16_t *hout, int one)
 {
     const int64_t e0 = P.row_ptr[base + r], e1 = P.row_ptr[base + r + 1];
     uint64_t aP = 0, aN = 0;
-    int32_t cP[8], cN[8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) { cP[k] = 0; cN[k] = 0; }
     int32_t nN = 0, cnt = 0;
+    int32_t cP0 = 0, cP1 = 0, cP2 = 0, cP3 = 0, cP4 = 0, cP5 = 0, cP6 = 0, cP7 = 0;
+    int32_t cN0 = 0, cN1 = 0, cN2 = 0, cN3 = 0, cN4 = 0, cN5 = 0, cN6 = 0, cN7 = 0;
+#define GDI_FLUSH()                                                                               \
+    do {                                                                                          \
+        cP0 += (int32_t)(aP & 0xFF); cP1 += (int32_t)((aP >> 8) & 0xFF);                          \
+        cP2 += (int32_t)((aP >> 16) & 0xFF); cP3 += (int32_t)((aP >> 24) & 0xFF);                 \
+        cP4 += (int32_t)((aP >> 32) & 0xFF); cP5 += (int32_t)((aP >> 40) & 0xFF);                 \
+        cP6 += (int32_t)((aP >> 48) & 0xFF); cP7 += (int32_t)((aP >> 56) & 0xFF);                 \
+        cN0 += (int32_t)(aN & 0xFF); cN1 += (int32_t)((aN >> 8) & 0xFF);                          \
+        cN2 += (int32_t)((aN >> 16) & 0xFF); cN3 += (int32_t)((aN >> 24) & 0xFF);                 \
+        cN4 += (int32_t)((aN >> 32) & 0xFF); cN5 += (int32_t)((aN >> 40) & 0xFF);                 \
+        cN6 += (int32_t)((aN >> 48) & 0xFF); cN7 += (int32_t)((aN >> 56) & 0xFF);                 \
+        aP = aN = 0;                                                                              \
+    } while (0)
     int64_t e = e0;
     for (; e + 4 <= e1; e += 4) {
         const uint32_t c0 = __ldg(P.col + e), c1 = __ldg(P.col + e + 1);
@@ -148,33 +159,34 @@ __device__ void field8_thread(const GdiDevProblem &P, int64_t base, int32_t r, c
         if (c2 >> 31) { aN += s2; ++nN; } else aP += s2;
         if (c3 >> 31) { aN += s3; ++nN; } else aP += s3;
         cnt += 4;
-        if (cnt >= 252) {
-#pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                cP[k] += (int32_t)((aP >> (8 * k)) & 0xFF);
-                cN[k] += (int32_t)((aN >> (8 * k)) & 0xFF);
-            }
-            aP = aN = 0;
-            cnt = 0;
-        }
+        if (cnt >= 252) { GDI_FLUSH(); cnt = 0; }
     }
     for (; e < e1; ++e) {
         const uint32_t c = __ldg(P.col + e);
         const uint64_t sv = spread8(__ldcg(packed + base + (c & 0x7FFFFFFFu)));
         if (c >> 31) { aN += sv; ++nN; } else aP += sv;
     }
-    const int32_t nP = (int32_t)(e1 - e0) - nN;
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-        cP[k] += (int32_t)((aP >> (8 * k)) & 0xFF);
-        cN[k] += (int32_t)((aN >> (8 * k)) & 0xFF);
-        h[k] = (nP - nN) - 2 * (cP[k] - cN[k]);   // sum w (1 - 2 bit) = sum w - 2 sum w bit
+    GDI_FLUSH();
+#undef GDI_FLUSH
+    const int32_t sw = (int32_t)(e1 - e0) - 2 * nN;     // sum of weights
+    // h = sum w (1 - 2 bit) = sum w - 2 sum w bit
+    if (one < 0) {
+        hout[0] = (int16_t)(sw - 2 * (cP0 - cN0)); hout[1] = (int16_t)(sw - 2 * (cP1 - cN1));
+        hout[2] = (int16_t)(sw - 2 * (cP2 - cN2)); hout[3] = (int16_t)(sw - 2 * (cP3 - cN3));
+        hout[4] = (int16_t)(sw - 2 * (cP4 - cN4)); hout[5] = (int16_t)(sw - 2 * (cP5 - cN5));
+        hout[6] = (int16_t)(sw - 2 * (cP6 - cN6)); hout[7] = (int16_t)(sw - 2 * (cP7 - cN7));
+    } else {
+        const int32_t cp = one == 0 ? cP0 : one == 1 ? cP1 : one == 2 ? cP2 : one == 3 ? cP3
+                         : one == 4 ? cP4 : one == 5 ? cP5 : one == 6 ? cP6 : cP7;
+        const int32_t cn = one == 0 ? cN0 : one == 1 ? cN1 : one == 2 ? cN2 : one == 3 ? cN3
+                         : one == 4 ? cN4 : one == 5 ? cN5 : one == 6 ? cN6 : cN7;
+        hout[0] = (int16_t)(sw - 2 * (cp - cn));
     }
 }
 
 // Partial sums of one chunk [c0, c1) of a long row, by one warp: sw = sum of weights,
 // sb[k] = sum of w * bit_k (bit_k set = replica k is -1); valid in every lane.
-__device__ void chunk8_warp(const GdiDevProblem &P, int64_t base, int64_t c0, int64_t c1,
+__device__ __forceinline__ void chunk8_warp(const GdiDevProblem &P, int64_t base, int64_t c0, int64_t c1,
                             const uint8_t *packed, int32_t &sw, int32_t sb[8])
 {
     const int lane = threadIdx.x & 31;
@@ -424,16 +436,7 @@ __device__ void range_thresholds(const GridArgs &A, const GSmem &S, int32_t a0, 
         if (all_reps && deg > LONG_ROW) {
             S.longq[atomicAdd(&nlong, 1)] = i;
         } else {
-            int32_t h[8];
-            field8_thread(P, base, rk, packed, h);
-            if (all_reps) {
-#pragma unroll
-                for (int k = 0; k < 8; ++k) hbuf[(size_t)i * 8 + k] = (int16_t)h[k];
-            } else {
-#pragma unroll
-                for (int k = 0; k < 8; ++k)
-                    if (k == one) hbuf[i] = (int16_t)h[k];
-            }
+            field8_thread(P, base, rk, packed, all_reps ? hbuf + (size_t)i * 8 : hbuf + i, all_reps ? -1 : one);
         }
     }
     __syncthreads();
@@ -485,6 +488,7 @@ __device__ void range_thresholds(const GridArgs &A, const GSmem &S, int32_t a0, 
     if (ns > 0) {
         const int32_t q0 = a0 >> 2, q1 = (a1 - 1) >> 2;
         const int nr = all_reps ? A.nrep : 1;
+        const int a_shift = (P.A > 0 && (P.A & (P.A - 1)) == 0) ? 2 + __ffs(P.A) - 1 : -1;   // log2(4A)
         const int64_t tasks = (int64_t)(q1 - q0 + 1) * nr;
         for (int64_t t = threadIdx.x; t < tasks; t += GB) {
             const int32_t qd = q0 + (int32_t)(t / nr);
@@ -500,7 +504,8 @@ __device__ void range_thresholds(const GridArgs &A, const GSmem &S, int32_t a0, 
                 const int sg = ((s0_out[i] >> r) & 1) ? -1 : 1;
                 const int32_t h = hbuf[(size_t)i * hs + (all_reps ? r : 0)];
                 const int32_t es = estar_of(S.row, rlen, A.R.mode, word_of(u4, j), Tsw);
-                gam_out[(size_t)i * hs + (all_reps ? r : 0)] = gamma_of(sg, h, es, P.A, P.B);
+                gam_out[(size_t)i * hs + (all_reps ? r : 0)] =
+                    a_shift >= 0 ? gamma_of_shift(sg, h, es, P.A, P.B, a_shift) : gamma_of(sg, h, es, P.A, P.B);
             }
         }
     }
@@ -605,9 +610,10 @@ __global__ void __launch_bounds__(GB, 1) gdi_grid_anneal_kernel(GridArgs A)
 #pragma unroll
             for (int k = 0; k < 8; ++k) cntm[k] += (b >> k) & 1;
         }
-        for (int k = 0; k < nrep; ++k) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
             const int32_t m = warp_sum(cntm[k]);
-            if (lane == 0 && m) atomicAdd(&X.Gcls[k], -2 * m);
+            if (k < nrep && lane == 0 && m) atomicAdd(&X.Gcls[k], -2 * m);
         }
         if (p == 0 && threadIdx.x < nrep) atomicAdd(&X.Gcls[threadIdx.x], n);
     }
@@ -761,8 +767,9 @@ __global__ void __launch_bounds__(GB, 1) gdi_grid_anneal_kernel(GridArgs A)
             for (int k = 0; k < 8; ++k) { dg[k] = 0; ct[k] = 0; }
             for (int32_t i = r0 + threadIdx.x; i < r1; i += GB) {
                 const uint8_t b = __ldcg(X.packed + base + i);
-                for (int k = 0; k < nrep; ++k)
-                    if (!((b >> k) & 1))
+#pragma unroll
+                for (int k = 0; k < 8; ++k)
+                    if (k < nrep && !((b >> k) & 1))
                         dg[k] += splitmix64_fin((uint64_t)(uint32_t)i | ((uint64_t)(sw & 0xFFFF) << 32) |
                                                 ((uint64_t)((A.rep_base + k) & 0xFFFF) << 48));
                 const int64_t e0 = P.row_ptr[base + i], e1 = P.row_ptr[base + i + 1];
@@ -772,15 +779,17 @@ __global__ void __launch_bounds__(GB, 1) gdi_grid_anneal_kernel(GridArgs A)
                     if ((int32_t)j <= i) continue;
                     const uint8_t d = b ^ __ldcg(X.packed + base + j);
                     if (!d) continue;
-                    for (int k = 0; k < nrep; ++k)
+#pragma unroll
+                    for (int k = 0; k < 8; ++k)
                         if ((d >> k) & 1) ct[k] += (cc >> 31) ? -1 : 1;
                 }
             }
-            for (int k = 0; k < nrep; ++k) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
                 const uint64_t a = warp_sum(dg[k]);
                 const int64_t b = warp_sum(ct[k]);
                 const int64_t o = (int64_t)(A.rep_base + k) * R.sweeps + sw;
-                if (lane == 0) {
+                if (k < nrep && lane == 0) {
                     if (a) atomicAdd((unsigned long long *)(R.tr_digest + o), (unsigned long long)a);
                     if (b) atomicAdd((unsigned long long *)(R.tr_cut + o), (unsigned long long)b);
                 }
