@@ -629,8 +629,7 @@ int gdi_anneal(gdi_ctx *c, const gdi_schedule *S, const gdi_run *run)
         int spc = 0, wpc = 0;
         size_t smem = 0;
         const int nblk = c->grid_limit > 0 ? std::min(c->grid_limit, sms) : sms;
-        if (gdi_grid_plan(P, max_row, nblk, &spc, &wpc, &smem) != 0 || smem > (size_t)max_optin ||
-            !gdi_grid_fallback_fits(spc))
+        if (gdi_grid_plan(P, max_row, nblk, &spc, &wpc, &smem) != 0 || smem > (size_t)max_optin)
             return fail(GDI_ERR_TOO_LARGE, "grid-scale plan needs " + std::to_string(smem) +
                                                " bytes of shared memory per block; use a smaller W");
         const int D = c->max_degree;

@@ -414,11 +414,13 @@ __device__ inline void class_partition(int32_t lo, int32_t hi, int W, int p, int
     nwin = k1 - k0;
 }
 
-// Thresholds of the spin range [a0, a1).  all_reps: every replica, stored [i*8 + r] (fields in
-// hbuf [i*8 + r], rows longer than LONG_ROW summed by a warp).  Otherwise only replica `one`,
-// stored [i] with fields [i] (thread-serial rows; used by the rare exact fallback).
+// Thresholds of the spin range [a0, a1).  all_reps: every replica, threshold of (i, r) stored at
+// gam_out[i * gis + r * grs] (fields in hbuf [i*8 + r], rows longer than LONG_ROW summed by a
+// warp).  Otherwise only replica `one`, stored at gam_out[i * gis] with fields [i] (thread-serial
+// rows; used by the rare exact fallback).  gam_out must hold 8 ints per rank either way (the
+// long-row partial sums live there before the thresholds are written).
 __device__ void range_thresholds(const GridArgs &A, const GSmem &S, int32_t a0, int32_t a1, int sw,
-                                 bool all_reps, int one, int32_t *gam_out, uint8_t *s0_out,
+                                 bool all_reps, int one, int32_t *gam_out, int gis, int grs, uint8_t *s0_out,
                                  int16_t *hbuf, int32_t rlen, float Tsw)
 {
     const GdiDevProblem &P = A.P;
@@ -504,7 +506,7 @@ __device__ void range_thresholds(const GridArgs &A, const GSmem &S, int32_t a0, 
                 const int sg = ((s0_out[i] >> r) & 1) ? -1 : 1;
                 const int32_t h = hbuf[(size_t)i * hs + (all_reps ? r : 0)];
                 const int32_t es = estar_of(S.row, rlen, A.R.mode, word_of(u4, j), Tsw);
-                gam_out[(size_t)i * hs + (all_reps ? r : 0)] =
+                gam_out[(size_t)i * gis + (size_t)(all_reps ? r : 0) * grs] =
                     a_shift >= 0 ? gamma_of_shift(sg, h, es, P.A, P.B, a_shift) : gamma_of(sg, h, es, P.A, P.B);
             }
         }
@@ -570,6 +572,74 @@ __device__ int32_t window_exact(const int32_t *gam, int gs, int gc, const uint8_
     return plus_first ? g + 2 * K2 : g - 2 * K2;
 }
 
+// G of every replica: n - 2 #(-1), accumulated into X.Gcls (zeroed by the host)
+__device__ void init_G(const GridArgs &A, int p, int Pb, int32_t n, int64_t base)
+{
+    const GdiGridScratch &X = A.X;
+    const int lane = threadIdx.x & 31;
+    const int nrep = A.nrep;
+    int32_t cntm[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    const int32_t r0 = (int32_t)(((int64_t)p * n) / Pb), r1 = (int32_t)(((int64_t)(p + 1) * n) / Pb);
+    for (int32_t i = r0 + threadIdx.x; i < r1; i += GB) {
+        const uint8_t b = __ldcg(X.packed + base + i);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) cntm[k] += (b >> k) & 1;
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const int32_t m = warp_sum(cntm[k]);
+        if (k < nrep && lane == 0 && m) atomicAdd(&X.Gcls[k], -2 * m);
+    }
+    if (p == 0 && threadIdx.x < nrep) atomicAdd(&X.Gcls[threadIdx.x], n);
+}
+
+// digest and cut of every replica after sweep sw (grid-wide atomics), and G after the sweep
+__device__ void sweep_trace(const GridArgs &A, int p, int Pb, int32_t n, int64_t base, int sw)
+{
+    const GdiDevProblem &P = A.P;
+    const GdiDevRun &R = A.R;
+    const GdiGridScratch &X = A.X;
+    const int lane = threadIdx.x & 31;
+    const int nrep = A.nrep;
+    const int32_t r0 = (int32_t)(((int64_t)p * n) / Pb), r1 = (int32_t)(((int64_t)(p + 1) * n) / Pb);
+    uint64_t dg[8];
+    int64_t ct[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) { dg[k] = 0; ct[k] = 0; }
+    for (int32_t i = r0 + threadIdx.x; i < r1; i += GB) {
+        const uint8_t b = __ldcg(X.packed + base + i);
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            if (k < nrep && !((b >> k) & 1))
+                dg[k] += splitmix64_fin((uint64_t)(uint32_t)i | ((uint64_t)(sw & 0xFFFF) << 32) |
+                                        ((uint64_t)((A.rep_base + k) & 0xFFFF) << 48));
+        const int64_t e0 = P.row_ptr[base + i], e1 = P.row_ptr[base + i + 1];
+        for (int64_t e = e0; e < e1; ++e) {
+            const uint32_t cc = __ldg(P.col + e);
+            const uint32_t j = cc & 0x7FFFFFFFu;
+            if ((int32_t)j <= i) continue;
+            const uint8_t d = b ^ __ldcg(X.packed + base + j);
+            if (!d) continue;
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                if ((d >> k) & 1) ct[k] += (cc >> 31) ? -1 : 1;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const uint64_t a = warp_sum(dg[k]);
+        const int64_t b = warp_sum(ct[k]);
+        const int64_t o = (int64_t)(A.rep_base + k) * R.sweeps + sw;
+        if (k < nrep && lane == 0) {
+            if (a) atomicAdd((unsigned long long *)(R.tr_digest + o), (unsigned long long)a);
+            if (b) atomicAdd((unsigned long long *)(R.tr_cut + o), (unsigned long long)b);
+        }
+    }
+    if (p == 0 && threadIdx.x < nrep)
+        R.tr_G[(int64_t)(A.rep_base + threadIdx.x) * R.sweeps + sw] =
+            *(volatile int32_t *)&X.Gcls[threadIdx.x];
+}
+
 __global__ void __launch_bounds__(GB, 1) gdi_grid_anneal_kernel(GridArgs A)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -601,22 +671,7 @@ __global__ void __launch_bounds__(GB, 1) gdi_grid_anneal_kernel(GridArgs A)
     const int W = P.W;
     const int nrep = A.nrep;
 
-    // G of every replica: n - 2 #(-1)   (X.Gcls zeroed by the host)
-    {
-        int32_t cntm[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        const int32_t r0 = (int32_t)(((int64_t)p * n) / Pb), r1 = (int32_t)(((int64_t)(p + 1) * n) / Pb);
-        for (int32_t i = r0 + threadIdx.x; i < r1; i += GB) {
-            const uint8_t b = __ldcg(X.packed + base + i);
-#pragma unroll
-            for (int k = 0; k < 8; ++k) cntm[k] += (b >> k) & 1;
-        }
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const int32_t m = warp_sum(cntm[k]);
-            if (k < nrep && lane == 0 && m) atomicAdd(&X.Gcls[k], -2 * m);
-        }
-        if (p == 0 && threadIdx.x < nrep) atomicAdd(&X.Gcls[threadIdx.x], n);
-    }
+    init_G(A, p, Pb, n, base);
     if (!grid_sync(X)) return;
 
     for (int sw = R.s_begin; sw < R.s_end; ++sw) {
@@ -633,7 +688,7 @@ __global__ void __launch_bounds__(GB, 1) gdi_grid_anneal_kernel(GridArgs A)
             class_partition(lo, hi, W, p, Pb, a0, a1, nwin);
             if (threadIdx.x < nrep) Gc[threadIdx.x] = *(volatile int32_t *)&X.Gcls[threadIdx.x];
             // ---- phase A: thresholds of my windows, window tables, block table
-            range_thresholds(A, S, a0, a1, sw, true, 0, S.gam, S.s0, S.h, rlen, Tsw);
+            range_thresholds(A, S, a0, a1, sw, true, 0, S.gam, 8, 1, S.s0, S.h, rlen, Tsw);
             for (int task = warp; task < nwin * nrep; task += NWARP) {
                 const int kk = task / nrep, r = task % nrep;
                 const int ws = kk * W, we = min(ws + W, a1 - a0);
@@ -703,7 +758,7 @@ __global__ void __launch_bounds__(GB, 1) gdi_grid_anneal_kernel(GridArgs A)
                     int16_t *fh = reinterpret_cast<int16_t *>(fg + nb);
                     uint8_t *fs = reinterpret_cast<uint8_t *>(fh + ((nb + 7) & ~7));
                     int32_t *fbins = reinterpret_cast<int32_t *>(fs + ((nb + 15) & ~15));
-                    range_thresholds(A, S, b0, b1, sw, false, r, fg, fs, fh, rlen, Tsw);
+                    range_thresholds(A, S, b0, b1, sw, false, r, fg, 1, 0, fs, fh, rlen, Tsw);
                     if (warp == 0) {
                         int32_t gg = g;
                         for (int kk = 0; kk < nw2; ++kk) {
@@ -758,45 +813,416 @@ __global__ void __launch_bounds__(GB, 1) gdi_grid_anneal_kernel(GridArgs A)
             }
             if (!grid_sync(X)) return;
         }
+        if (R.flags & GDI_DEV_TRACE) sweep_trace(A, p, Pb, n, base, sw);
+    }
+}
+
+// =============================================================================================
+// Sorted-window path (1 <= W <= 256).
+//
+// One warp takes one (window, replica): lanes hold the window's members (up to 8 per lane) with
+// keys (group, threshold distance from the class-start G c, position), and a bitonic sort puts
+// each group in its flip order.  The k-th member of the +1 group (gamma ascending) flips iff
+// G - 2k >= gamma_(k), i.e. iff a_k = gamma_(k) + 2k <= G; a_k is strictly increasing, so for any
+// entering G the flips are exactly the members with a_k <= G -- one comparison per member, no
+// histogram.  The -1 group likewise flips iff b_k = gamma'_(k) - 2k >= G.  Every member keeps
+// rel = a_k - c (or b_k - c) in shared memory; the exact replay of a window is then two warp
+// counts.
+//
+// Block maps: on the lattice x = G - c in {-64, -62, ..., 62} (64 points; G - c is always even) a
+// group is a staircase: index j -> ylo + popcount(mask & bits below j), read from where the a_k
+// (b_k) fall.  The maps of a block's windows are composed per replica into a 64-entry byte table
+// (-1 = leaves the lattice) and published with a release flag.  Every block then walks the tables
+// of the blocks before it (acquire loads) from c and gets its exact entering G without a grid
+// barrier.  Where the walk leaves the lattice, the block whose table failed publishes its exact
+// outgoing G (it knows its own entering G and replays exactly), and the walk continues from it.
+// One grid barrier per class remains: the next class reads this class's spins.
+constexpr int SMAXW = 256;
+constexpr int NT = 64;
+constexpr int32_t KEY_D = 1 << 22;      // threshold distances are clamped to [-KEY_D, KEY_D)
+constexpr int32_t REL_CAP = 32767;      // rel values are stored clamped to +-REL_CAP
+constexpr int32_t FAST_X = 32000;       // |G - c| up to which the stored rel values decide exactly
+constexpr unsigned long long STEP_MASK = (1ull << (NT - 1)) - 1ull;
+
+struct StageMap {
+    unsigned long long mask;            // bit j: the step from lattice point j to j + 1 rises
+    int32_t ylo;                        // output index of lattice point 0
+    int32_t pad;
+};
+
+struct SortedLayout {
+    size_t off_h, off_gam, off_s0, off_fm, off_longq, off_smap, off_hist, off_walk, off_row, off_misc,
+        total;
+};
+
+__host__ __device__ inline SortedLayout sorted_layout(int spc, int wpc, int max_row)
+{
+    SortedLayout L;
+    size_t o = 0;
+    L.off_h = o; o = align16(o + (size_t)spc * 8 * sizeof(int16_t));      // fields, then rel
+    L.off_gam = o; o = align16(o + (size_t)spc * 8 * sizeof(int32_t));    // thresholds [r][spc]
+    L.off_s0 = o; o = align16(o + (size_t)spc);
+    L.off_fm = o; o = align16(o + (size_t)((spc + 3) / 4) * sizeof(uint32_t));
+    L.off_longq = o; o = align16(o + (size_t)spc * sizeof(int32_t));
+    L.off_smap = o; o = align16(o + (size_t)wpc * 8 * 2 * sizeof(StageMap));
+    L.off_hist = o; o = align16(o + (size_t)NWARP * 2 * HB * sizeof(int32_t));
+    L.off_walk = o; o = align16(o + (size_t)8 * 32 * NT);
+    L.off_row = o; o = align16(o + (size_t)(max_row + 4) * sizeof(uint32_t));
+    L.off_misc = o; o = align16(o + 64 * sizeof(int64_t));
+    L.total = o;
+    return L;
+}
+
+// chain buffers carved from the scratch table area: exact outgoing G [P][8] (epoch << 32 | G),
+// table-ready flags [P], byte tables [P][8][64]
+__host__ __device__ inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+__host__ __device__ inline size_t chain_off_flag(int P) { return align256((size_t)P * 8 * sizeof(uint64_t)); }
+__host__ __device__ inline size_t chain_off_tab(int P) { return chain_off_flag(P) + align256((size_t)P * sizeof(uint32_t)); }
+__host__ __device__ inline size_t chain_bytes(int P) { return chain_off_tab(P) + (size_t)P * 8 * NT; }
+
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t *p)
+{
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p)
+{
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_u32(uint32_t *p, uint32_t v)
+{
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void st_release_u64(unsigned long long *p, unsigned long long v)
+{
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// bounded waits: false (error word set) after SPIN_LIMIT polls or when another block failed
+__device__ __forceinline__ bool wait_flag(const uint32_t *f, uint32_t want, const GdiGridScratch &X)
+{
+    long long spins = 0;
+    while (ld_acquire_u32(f) != want) {
+        if (++spins > SPIN_LIMIT) { atomicExch(X.err, GDI_DEVERR_TIMEOUT); return false; }
+        if ((spins & 63) == 0 && *(volatile int *)X.err) return false;
+        __nanosleep(32);
+    }
+    return true;
+}
+
+__device__ __forceinline__ bool wait_exact(const unsigned long long *f, uint32_t epoch, const GdiGridScratch &X,
+                                           int32_t &g)
+{
+    long long spins = 0;
+    unsigned long long v;
+    while (((v = ld_acquire_u64(f)) >> 32) != epoch) {
+        if (++spins > SPIN_LIMIT) { atomicExch(X.err, GDI_DEVERR_TIMEOUT); return false; }
+        if ((spins & 63) == 0 && *(volatile int *)X.err) return false;
+        __nanosleep(32);
+    }
+    g = (int32_t)(uint32_t)v;
+    return true;
+}
+
+// ascending bitonic sort of 32 * S keys held as key[s] of lane l = element l * S + s
+template <int S>
+__device__ __forceinline__ void warp_bitonic(uint32_t (&key)[S])
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int size = 2; size <= 32 * S; size <<= 1) {
+#pragma unroll
+        for (int j = size >> 1; j >= 1; j >>= 1) {
+            if (j >= S) {
+#pragma unroll
+                for (int s = 0; s < S; ++s) {
+                    const uint32_t o = __shfl_xor_sync(0xFFFFFFFFu, key[s], j / S);
+                    const int e = lane * S + s;
+                    const bool keep_min = ((e & j) == 0) == ((e & size) == 0);
+                    key[s] = keep_min ? min(key[s], o) : max(key[s], o);
+                }
+            } else {
+#pragma unroll
+                for (int s = 0; s < S; ++s) {
+                    if ((s & j) == 0) {
+                        const int e = lane * S + s;
+                        const uint32_t a = key[s], b = key[s + j];
+                        const bool swap = ((e & size) == 0) ? (a > b) : (a < b);
+                        key[s] = swap ? b : a;
+                        key[s + j] = swap ? a : b;
+                    }
+                }
+            }
+        }
+    }
+}
+
+// rel values and the two stage maps of one window (positions [ws, ws + wlen), wlen <= 32 * S) for
+// replica r, by one warp.  out[0] = +1 group, out[1] = -1 group.
+template <int S>
+__device__ __forceinline__ void window_maps(const int32_t *gam_r, const uint8_t *s0, int16_t *rel_r, int ws,
+                                            int wlen, int r, int32_t c, StageMap *out)
+{
+    const int lane = threadIdx.x & 31;
+    uint32_t key[S];
+    int32_t np = 0;
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+        const int pos = s * 32 + lane;
+        uint32_t k = 0xFFFFFFFFu;
+        if (pos < wlen) {
+            const int32_t g = gam_r[ws + pos];
+            const uint32_t neg = (s0[ws + pos] >> r) & 1u;
+            int32_t d = neg ? c - g : g - c;
+            d = min(max(d, -KEY_D), KEY_D - 1);
+            k = (neg << 31) | ((uint32_t)(d + KEY_D) << 8) | (uint32_t)pos;
+            np += neg ? 0 : 1;
+        }
+        key[s] = k;
+    }
+    np = __reduce_add_sync(0xFFFFFFFFu, np);
+    warp_bitonic<S>(key);
+    uint32_t kp0 = 0, kp1 = 0, km0 = 0, km1 = 0;
+    int32_t cle = 0, cge = 0;
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+        const int e = lane * S + s;
+        if (e < wlen) {
+            const uint32_t k = key[s];
+            const bool neg = (k >> 31) != 0;
+            const int32_t d = (int32_t)((k >> 8) & 0x7FFFFFu) - KEY_D;
+            const int pos = (int)(k & 0xFFu);
+            const int32_t rel = neg ? -d - 2 * (e - np) : d + 2 * e;
+            rel_r[ws + pos] = (int16_t)min(max(rel, -REL_CAP), REL_CAP);
+            if (!neg) {
+                if (rel <= -NT) {
+                    ++cle;
+                } else if (rel <= NT - 2) {
+                    const int b = (rel + NT - 1) >> 1;
+                    if (b < 32) kp0 |= 1u << b; else kp1 |= 1u << (b - 32);
+                }
+            } else if (rel >= -NT) {
+                ++cge;
+                if (rel <= NT - 3) {
+                    const int b = (rel + NT) >> 1;
+                    if (b < 32) km0 |= 1u << b; else km1 |= 1u << (b - 32);
+                }
+            }
+        }
+    }
+    kp0 = __reduce_or_sync(0xFFFFFFFFu, kp0);
+    kp1 = __reduce_or_sync(0xFFFFFFFFu, kp1);
+    km0 = __reduce_or_sync(0xFFFFFFFFu, km0);
+    km1 = __reduce_or_sync(0xFFFFFFFFu, km1);
+    cle = __reduce_add_sync(0xFFFFFFFFu, cle);
+    cge = __reduce_add_sync(0xFFFFFFFFu, cge);
+    if (lane == 0) {
+        out[0].mask = ~(((unsigned long long)kp1 << 32) | kp0) & STEP_MASK;
+        out[0].ylo = -cle;
+        out[1].mask = ~(((unsigned long long)km1 << 32) | km0) & STEP_MASK;
+        out[1].ylo = cge;
+    }
+}
+
+__device__ __forceinline__ int stage_apply(const StageMap &m, int t)
+{
+    if (t < 0) return -1;
+    const int y = m.ylo + __popcll(m.mask & ((1ull << t) - 1ull));
+    return (y >= 0 && y < NT) ? y : -1;
+}
+
+__global__ void __launch_bounds__(GB, 1) gdi_grid_sorted_kernel(GridArgs A)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const GdiDevProblem &P = A.P;
+    const GdiDevRun &R = A.R;
+    const GdiGridScratch &X = A.X;
+    const int Pb = gridDim.x, p = blockIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int spc = A.spc;
+    const SortedLayout L = sorted_layout(spc, A.wpc, R.max_row);
+    int16_t *hb = reinterpret_cast<int16_t *>(smem_raw + L.off_h);   // fields [i*8 + r], then rel [r*spc + i]
+    int32_t *gam = reinterpret_cast<int32_t *>(smem_raw + L.off_gam);
+    uint8_t *s0 = smem_raw + L.off_s0;
+    uint32_t *fm = reinterpret_cast<uint32_t *>(smem_raw + L.off_fm);
+    StageMap *smap = reinterpret_cast<StageMap *>(smem_raw + L.off_smap);
+    int32_t *hist = reinterpret_cast<int32_t *>(smem_raw + L.off_hist);
+    int8_t *walk = reinterpret_cast<int8_t *>(smem_raw + L.off_walk);
+    GSmem S = {};
+    S.longq = reinterpret_cast<int32_t *>(smem_raw + L.off_longq);
+    S.hist = hist;
+    S.row = reinterpret_cast<uint32_t *>(smem_raw + L.off_row);
+    S.misc = reinterpret_cast<int64_t *>(smem_raw + L.off_misc);
+    int32_t *Gc = reinterpret_cast<int32_t *>(S.misc);   // [8] class-start G of each replica
+    unsigned char *cb = reinterpret_cast<unsigned char *>(X.tables);
+    unsigned long long *exg = reinterpret_cast<unsigned long long *>(cb);
+    uint32_t *flag = reinterpret_cast<uint32_t *>(cb + chain_off_flag(Pb));
+    int8_t *tabs = reinterpret_cast<int8_t *>(cb + chain_off_tab(Pb));
+    const int64_t base = P.node_off[0];
+    const int32_t n = (int32_t)(P.node_off[1] - base);
+    const int32_t *cls = P.class_ptr + P.class_off[0];
+    const int32_t ncls = P.class_off[1] - P.class_off[0] - 1;
+    const int W = P.W;
+    const int nrep = A.nrep;
+    const int SL = W <= 32 ? 1 : W <= 64 ? 2 : W <= 128 ? 4 : 8;
+
+    init_G(A, p, Pb, n, base);
+    if (!grid_sync(X)) return;
+
+    uint32_t epoch = 0;
+    for (int sw = R.s_begin; sw < R.s_end; ++sw) {
+        const int32_t roff = R.tab_off[sw];
+        const int32_t rlen = R.tab_off[sw + 1] - roff;
+        for (int k = threadIdx.x; k < rlen; k += GB) S.row[k] = R.tab[roff + k];
+        const float Tsw = R.temp ? R.temp[sw] : 0.f;
+        const bool plus_first = (sw & 1) == 0;
+        __syncthreads();
+        for (int c = 0; c < ncls; ++c) {
+            ++epoch;
+            const int32_t lo = cls[c], hi = cls[c + 1];
+            int32_t a0, a1;
+            int nwin;
+            class_partition(lo, hi, W, p, Pb, a0, a1, nwin);
+            const int32_t ns = a1 - a0;
+            if (threadIdx.x < nrep) Gc[threadIdx.x] = *(volatile int32_t *)&X.Gcls[threadIdx.x];
+            // ---- thresholds of my ranks (ends with a block barrier)
+            range_thresholds(A, S, a0, a1, sw, true, 0, gam, 1, spc, s0, hb, rlen, Tsw);
+            // ---- sorted groups: rel values and stage maps of every (window, replica)
+            for (int task = warp; task < nwin * nrep; task += NWARP) {
+                const int kk = task / nrep, r = task % nrep;
+                const int ws = kk * W, wlen = min(W, ns - ws);
+                const int32_t *gr = gam + (size_t)r * spc;
+                int16_t *rr = hb + (size_t)r * spc;
+                StageMap *o = smap + ((size_t)kk * 8 + r) * 2;
+                if (SL == 1) window_maps<1>(gr, s0, rr, ws, wlen, r, Gc[r], o);
+                else if (SL == 2) window_maps<2>(gr, s0, rr, ws, wlen, r, Gc[r], o);
+                else if (SL == 4) window_maps<4>(gr, s0, rr, ws, wlen, r, Gc[r], o);
+                else window_maps<8>(gr, s0, rr, ws, wlen, r, Gc[r], o);
+            }
+            for (int i = threadIdx.x; i < (ns + 3) / 4; i += GB) fm[i] = 0;
+            __syncthreads();
+            // ---- block table per replica: lanes hold lattice points lane and lane + 32
+            int t0 = lane, t1 = lane + 32;
+            if (warp < nrep) {
+                const int r = warp;
+                for (int kk = 0; kk < nwin; ++kk) {
+#pragma unroll
+                    for (int ph = 0; ph < 2; ++ph) {
+                        const StageMap m = smap[((size_t)kk * 8 + r) * 2 + (plus_first ? ph : 1 - ph)];
+                        t0 = stage_apply(m, t0);
+                        t1 = stage_apply(m, t1);
+                    }
+                }
+                int8_t *dst = tabs + ((size_t)p * 8 + r) * NT;
+                dst[lane] = (int8_t)t0;
+                dst[lane + 32] = (int8_t)t1;
+                __threadfence();
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) st_release_u32(flag + p, epoch);
+            // ---- entering G: walk the tables of blocks 0 .. p-1 from c; then the exact replay
+            if (warp < nrep) {
+                const int r = warp;
+                const int32_t c0 = Gc[r];
+                int8_t *wb = walk + (size_t)r * 32 * NT;
+                int idx = NT / 2;          // lattice index of the running G, or -1 when off the lattice
+                int32_t gx = c0;           // the running G when off the lattice
+                bool ok = true;
+                for (int j0 = 0; j0 < p && ok; j0 += 32) {
+                    const int j = j0 + lane;
+                    bool mine = true;
+                    if (j < p) {
+                        mine = wait_flag(flag + j, epoch, X);
+                        if (mine) {
+                            const uint4 *src = reinterpret_cast<const uint4 *>(tabs + ((size_t)j * 8 + r) * NT);
+                            const uint4 v0 = __ldcg(src), v1 = __ldcg(src + 1), v2 = __ldcg(src + 2),
+                                        v3 = __ldcg(src + 3);
+                            uint4 *d4 = reinterpret_cast<uint4 *>(wb + (size_t)lane * NT);
+                            d4[0] = v0;
+                            d4[1] = v1;
+                            d4[2] = v2;
+                            d4[3] = v3;
+                        }
+                    }
+                    ok = __all_sync(0xFFFFFFFFu, mine);
+                    __syncwarp();
+                    if (!ok) break;
+                    const int nb = min(32, p - j0);
+                    for (int l = 0; l < nb && ok; ++l) {
+                        const int nidx = idx >= 0 ? (int)wb[l * NT + idx] : -1;
+                        if (nidx >= 0) { idx = nidx; continue; }
+                        int32_t v = 0;
+                        ok = wait_exact(exg + (size_t)(j0 + l) * 8 + r, epoch, X, v);
+                        gx = v;
+                        const int32_t xr = gx - c0;
+                        idx = (xr >= -NT && xr <= NT - 2) ? (xr + NT) >> 1 : -1;
+                    }
+                    ok = __all_sync(0xFFFFFFFFu, ok);
+                    __syncwarp();
+                }
+                if (ok) {
+                    const int32_t gin = idx >= 0 ? c0 - NT + 2 * idx : gx;
+                    const int own = __shfl_sync(0xFFFFFFFFu, (idx >= 0 && idx < 32) ? t0 : t1, idx & 31);
+                    const bool need_exact = idx < 0 || own < 0;
+                    int32_t x = gin - c0;
+                    const int32_t *gr = gam + (size_t)r * spc;
+                    const int16_t *rr = hb + (size_t)r * spc;
+                    int32_t *bins = hist + (size_t)warp * 2 * HB;
+                    for (int kk = 0; kk < nwin; ++kk) {
+                        const int ws = kk * W, we = min(ws + W, ns);
+                        if (x >= -FAST_X && x <= FAST_X) {
+#pragma unroll
+                            for (int ph = 0; ph < 2; ++ph) {
+                                const bool plus = plus_first == (ph == 0);
+                                int32_t cnt = 0;
+                                for (int i = ws + lane; i < we; i += 32) {
+                                    const bool neg = (s0[i] >> r) & 1;
+                                    if (neg != plus) {
+                                        const int32_t rv = rr[i];
+                                        if (plus ? rv <= x : rv >= x) {
+                                            ++cnt;
+                                            atomicOr(&fm[i >> 2], 1u << (8 * (i & 3) + r));
+                                        }
+                                    }
+                                }
+                                cnt = __reduce_add_sync(0xFFFFFFFFu, cnt);
+                                x = plus ? x - 2 * cnt : x + 2 * cnt;
+                            }
+                        } else {
+                            int32_t g = c0 + x;
+                            const int32_t K1 = warp_group(gr, 1, 0, s0, r, ws, we, g, plus_first, bins, fm);
+                            g = plus_first ? g - 2 * K1 : g + 2 * K1;
+                            const int32_t K2 = warp_group(gr, 1, 0, s0, r, ws, we, g, !plus_first, bins, fm);
+                            g = plus_first ? g + 2 * K2 : g - 2 * K2;
+                            x = g - c0;
+                        }
+                    }
+                    const int32_t gout = c0 + x;
+                    if (lane == 0) {
+                        if (need_exact) {
+                            st_release_u64(exg + (size_t)p * 8 + r,
+                                           ((unsigned long long)epoch << 32) | (uint32_t)gout);
+                            atomicAdd(X.status + r, 1);
+                        }
+                        if (p == Pb - 1) X.Gcls[r] = gout;
+                    }
+                }
+            }
+            __syncthreads();
+            for (int32_t i = threadIdx.x; i < ns; i += GB) {
+                const uint8_t f = (uint8_t)(fm[i >> 2] >> (8 * (i & 3)));
+                if (f) X.packed[base + a0 + i] = s0[i] ^ f;
+            }
+            if (!grid_sync(X)) return;
+        }
         if (R.flags & GDI_DEV_TRACE) {
-            // digest and cut of every replica after this sweep (grid-wide atomics)
-            const int32_t r0 = (int32_t)(((int64_t)p * n) / Pb), r1 = (int32_t)(((int64_t)(p + 1) * n) / Pb);
-            uint64_t dg[8];
-            int64_t ct[8];
-#pragma unroll
-            for (int k = 0; k < 8; ++k) { dg[k] = 0; ct[k] = 0; }
-            for (int32_t i = r0 + threadIdx.x; i < r1; i += GB) {
-                const uint8_t b = __ldcg(X.packed + base + i);
-#pragma unroll
-                for (int k = 0; k < 8; ++k)
-                    if (k < nrep && !((b >> k) & 1))
-                        dg[k] += splitmix64_fin((uint64_t)(uint32_t)i | ((uint64_t)(sw & 0xFFFF) << 32) |
-                                                ((uint64_t)((A.rep_base + k) & 0xFFFF) << 48));
-                const int64_t e0 = P.row_ptr[base + i], e1 = P.row_ptr[base + i + 1];
-                for (int64_t e = e0; e < e1; ++e) {
-                    const uint32_t cc = __ldg(P.col + e);
-                    const uint32_t j = cc & 0x7FFFFFFFu;
-                    if ((int32_t)j <= i) continue;
-                    const uint8_t d = b ^ __ldcg(X.packed + base + j);
-                    if (!d) continue;
-#pragma unroll
-                    for (int k = 0; k < 8; ++k)
-                        if ((d >> k) & 1) ct[k] += (cc >> 31) ? -1 : 1;
-                }
-            }
-#pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                const uint64_t a = warp_sum(dg[k]);
-                const int64_t b = warp_sum(ct[k]);
-                const int64_t o = (int64_t)(A.rep_base + k) * R.sweeps + sw;
-                if (k < nrep && lane == 0) {
-                    if (a) atomicAdd((unsigned long long *)(R.tr_digest + o), (unsigned long long)a);
-                    if (b) atomicAdd((unsigned long long *)(R.tr_cut + o), (unsigned long long)b);
-                }
-            }
-            if (p == 0 && threadIdx.x < nrep)
-                R.tr_G[(int64_t)(A.rep_base + threadIdx.x) * R.sweeps + sw] =
-                    *(volatile int32_t *)&X.Gcls[threadIdx.x];
+            sweep_trace(A, p, Pb, n, base, sw);
+            // a block may start writing the next sweep's spins before every block has read this
+            // sweep's (it waits only for the blocks before it), so the trace gets its own barrier
+            if (!grid_sync(X)) return;
         }
     }
 }
@@ -983,14 +1409,6 @@ __global__ void repair_apply_kernel(int8_t *spins, int64_t N, int nrep, const ui
 }  // namespace
 
 // ---------------------------------------------------------------------------------------------
-int gdi_grid_fallback_fits(int spc)
-{
-    // the exact chain fallback keeps thresholds, fields, start signs and bins of one block's
-    // windows (one replica) in the histogram area
-    return (size_t)spc * 7 + 64 + HA * sizeof(int32_t) <= (size_t)NWARP * 2 * HB * sizeof(int32_t) &&
-           (size_t)spc <= (size_t)NWARP * 2 * HB;
-}
-
 int gdi_grid_plan(const GdiDevProblem &P, int max_row, int sms, int *spc, int *wpc, size_t *smem)
 {
     if (P.num_instances != 1 || P.W < 1) return -1;
@@ -999,6 +1417,15 @@ int gdi_grid_plan(const GdiDevProblem &P, int max_row, int sms, int *spc, int *w
     const int w = (wp + sms - 1) / sms;
     *wpc = w < 1 ? 1 : w;
     *spc = *wpc * P.W;
+    // long rows keep their chunk counts in the histogram area
+    if ((size_t)*spc > (size_t)NWARP * 2 * HB) return -1;
+    if (P.W <= SMAXW) {
+        *smem = sorted_layout(*spc, *wpc, max_row).total;
+        return 0;
+    }
+    // the exact chain fallback of the tabulated path keeps thresholds, fields, start signs and bins
+    // of one block's windows (one replica) in the histogram area
+    if ((size_t)*spc * 7 + 64 + HA * sizeof(int32_t) > (size_t)NWARP * 2 * HB * sizeof(int32_t)) return -1;
     *smem = grid_layout(*spc, *wpc, sms, max_row).total;
     return 0;
 }
@@ -1007,19 +1434,23 @@ int gdi_launch_grid_anneal(const GdiDevProblem &P, const GdiDevRun &R, const Gdi
                            int8_t *spins, int sms, int spc, int wpc, size_t smem, void *stream)
 {
     cudaStream_t st = (cudaStream_t)stream;
-    cudaError_t e = cudaFuncSetAttribute(gdi_grid_anneal_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    const bool sorted = P.W <= SMAXW;
+    const void *kern = sorted ? (const void *)gdi_grid_sorted_kernel : (const void *)gdi_grid_anneal_kernel;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return (int)e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gdi_grid_anneal_kernel, GB, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, GB, smem);
     if (e != cudaSuccess) return (int)e;
     if (per_sm < 1) return (int)cudaErrorCooperativeLaunchTooLarge;
+    // the sorted path's chain buffers (exact G, flags, byte tables) live in the table area
+    if (sorted && chain_bytes(sms) > (size_t)sms * 8 * TW * sizeof(int16_t)) return (int)cudaErrorInvalidValue;
     const int pg = (int)((P.N + 255) / 256) < 4096 ? (int)((P.N + 255) / 256) : 4096;
     for (int g0 = 0; g0 < P.replicas; g0 += 8) {
         const int nrep = P.replicas - g0 < 8 ? P.replicas - g0 : 8;
         pack_kernel<<<pg, 256, 0, st>>>(spins, P.N, g0, nrep, X.packed);
         cudaMemsetAsync(X.Gcls, 0, 8 * sizeof(int32_t), st);
         cudaMemsetAsync(X.bar, 0, 2 * sizeof(unsigned int), st);
+        if (sorted) cudaMemsetAsync(X.tables, 0, chain_off_tab(sms), st);
         GridArgs A;
         A.P = P;
         A.R = R;
@@ -1029,7 +1460,7 @@ int gdi_launch_grid_anneal(const GdiDevProblem &P, const GdiDevRun &R, const Gdi
         A.spc = spc;
         A.wpc = wpc;
         void *args[] = {&A};
-        e = cudaLaunchCooperativeKernel((const void *)gdi_grid_anneal_kernel, dim3(sms), dim3(GB), args, smem, st);
+        e = cudaLaunchCooperativeKernel(kern, dim3(sms), dim3(GB), args, smem, st);
         if (e != cudaSuccess) return (int)e;
         unpack_kernel<<<pg, 256, 0, st>>>(spins, P.N, g0, nrep, X.packed);
         e = cudaMemcpyAsync(R.raw_G + g0, X.Gcls, nrep * sizeof(int32_t), cudaMemcpyDeviceToDevice, st);
@@ -1070,4 +1501,3 @@ int gdi_launch_grid_finish(const GdiDevProblem &P, const GdiDevRun &R, const Gdi
     return (int)cudaGetLastError();
 }
 
-size_t gdi_grid_smem(int spc, int wpc, int P, int max_row) { return grid_layout(spc, wpc, P, max_row).total; }

@@ -28,7 +28,9 @@ struct GdiDevProblem {
 // Global scratch of the grid-scale path (single large instance).
 struct GdiGridScratch {
     uint8_t *packed;                 // [N] spins of one replica group: bit r set = replica r is -1
-    int16_t *tables;                 // [P][8][TW] composed window tables of every block
+    int16_t *tables;                 // [P][8][TW] composed window tables of every block (W > 256);
+                                     // for W <= 256 the same bytes hold the sorted path's exact-G
+                                     // words, table-ready flags and [P][8][64] byte tables
     int32_t *gin;                    // [P][8] exact G entering every block's windows
     int32_t *Gcls;                   // [8] G at class start / after the class
     unsigned int *bar;               // [2] grid barrier: arrival count, generation
@@ -75,8 +77,6 @@ int gdi_launch_cta_anneal(const GdiDevProblem &P, const GdiDevRun &R, int block,
                           void *stream, int *grid_used, size_t *smem_used);
 int gdi_cta_smem_bytes(const GdiDevProblem &P, const GdiDevRun &R, int block, size_t *bytes, int *hist);
 int gdi_grid_plan(const GdiDevProblem &P, int max_row, int sms, int *spc, int *wpc, size_t *smem);
-size_t gdi_grid_smem(int spc, int wpc, int P, int max_row);
-int gdi_grid_fallback_fits(int spc);
 int gdi_launch_grid_anneal(const GdiDevProblem &P, const GdiDevRun &R, const GdiGridScratch &X,
                            int8_t *spins, int sms, int spc, int wpc, size_t smem, void *stream);
 int gdi_launch_grid_finish(const GdiDevProblem &P, const GdiDevRun &R, const GdiGridScratch &X,

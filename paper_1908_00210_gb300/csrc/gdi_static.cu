@@ -119,8 +119,7 @@ extern "C" int gdi_anneal_static(int32_t n, const int64_t *row_ptr, const uint32
     P.max_class = max_class;
     int spc = 0, wpc = 0;
     size_t smem = 0;
-    if (gdi_grid_plan(P, max_row, nblk, &spc, &wpc, &smem) != 0 || smem > (size_t)optin ||
-        !gdi_grid_fallback_fits(spc))
+    if (gdi_grid_plan(P, max_row, nblk, &spc, &wpc, &smem) != 0 || smem > (size_t)optin)
         return gdi_set_error(GDI_ERR_TOO_LARGE, "gdi_anneal_static: the plan needs " + std::to_string(smem) +
                                                     " bytes of shared memory per block; use a smaller W");
 

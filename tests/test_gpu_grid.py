@@ -69,6 +69,36 @@ def test_grid_bad_start_takes_exact_fallback(gdi):
     assert launch["fallbacks"] > 0
 
 
+@pytest.mark.parametrize("W", [1, 3, 33, 200])
+def test_grid_sorted_window_sizes(gdi, W):
+    """Windows of 1 to 8 members per lane (and ragged last windows) on the sorted-window path."""
+    g = erdos_renyi(12000, 0.0008, 50 + W, signed=True)
+    grid_vs_oracle(gdi, g, W=W, sweeps=6, replicas=3)
+
+
+def test_grid_sorted_far_from_class_start(gdi):
+    """All spins +1 on 10^5 vertices: inside the first classes G moves by far more than the stored
+    window values cover (|G - c| > 32000), so windows replay through the exact counting path."""
+    g = barabasi_albert(100_000, 5, 51)
+    init = np.ones((2, g.n), dtype=np.int8)
+    launch = grid_vs_oracle(gdi, g, W=256, sweeps=2, replicas=2, init=init)
+    assert launch["fallbacks"] > 0
+
+
+@pytest.mark.parametrize("W", [300, 1024])
+def test_grid_tabulated_large_windows(gdi, W):
+    """W > 256 takes the tabulated-window path (histogram tables, chain blocks)."""
+    g = barabasi_albert(20000, 5, 52)
+    grid_vs_oracle(gdi, g, W=W, sweeps=8, replicas=5)
+
+
+def test_grid_tabulated_bad_start(gdi):
+    g = barabasi_albert(20000, 5, 53)
+    init = np.ones((3, g.n), dtype=np.int8)
+    launch = grid_vs_oracle(gdi, g, W=512, sweeps=3, replicas=3, init=init)
+    assert launch["fallbacks"] > 0
+
+
 def test_grid_ba_1m_first_sweeps(gdi):
     """The full-size workload (BA n = 10^6, m = 5, 8 replicas, W = 256, 500-sweep schedule), checked
     on its first 2 sweeps (then repaired) against the oracle."""
