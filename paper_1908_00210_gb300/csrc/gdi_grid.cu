@@ -831,10 +831,11 @@ __global__ void __launch_bounds__(GB, 1) gdi_grid_anneal_kernel(GridArgs A)
 //
 // Block maps: on the lattice x = G - c in {-64, -62, ..., 62} (64 points; G - c is always even) a
 // group is a staircase: index j -> ylo + popcount(mask & bits below j), read from where the a_k
-// (b_k) fall.  The maps of a block's windows are composed per replica into a 64-entry byte table
-// (-1 = leaves the lattice) and published with a release flag.  Every block then walks the tables
-// of the blocks before it (acquire loads) from c and gets its exact entering G without a grid
-// barrier.  Where the walk leaves the lattice, the block whose table failed publishes its exact
+// (b_k) fall.  The maps of a block's windows are composed per replica (64 lattice points, two per
+// lane); the composition is again a staircase on the interval of inputs that stay on the lattice,
+// published as 16 bytes (rise mask, value at the interval start, interval) with a release flag.
+// Every block then fetches the entries of the blocks before it (acquire loads, all at once) and
+// walks them from c to its exact entering G without a grid barrier.  Where the walk leaves the lattice, the block whose table failed publishes its exact
 // outgoing G (it knows its own entering G and replays exactly), and the walk continues from it.
 // One grid barrier per class remains: the next class reads this class's spins.
 constexpr int SMAXW = 256;
@@ -851,11 +852,12 @@ struct StageMap {
 };
 
 struct SortedLayout {
-    size_t off_h, off_gam, off_s0, off_fm, off_longq, off_smap, off_hist, off_walk, off_row, off_misc,
-        total;
+    size_t off_h, off_gam, off_s0, off_fm, off_fbits, off_longq, off_smap, off_hist, off_walk, off_row,
+        off_misc, total;
+    int fw;                             // words of one replica's flip bitmap
 };
 
-__host__ __device__ inline SortedLayout sorted_layout(int spc, int wpc, int max_row)
+__host__ __device__ inline SortedLayout sorted_layout(int spc, int wpc, int max_row, int P)
 {
     SortedLayout L;
     size_t o = 0;
@@ -863,10 +865,12 @@ __host__ __device__ inline SortedLayout sorted_layout(int spc, int wpc, int max_
     L.off_gam = o; o = align16(o + (size_t)spc * 8 * sizeof(int32_t));    // thresholds [r][spc]
     L.off_s0 = o; o = align16(o + (size_t)spc);
     L.off_fm = o; o = align16(o + (size_t)((spc + 3) / 4) * sizeof(uint32_t));
+    L.fw = spc / 32 + 2;
+    L.off_fbits = o; o = align16(o + (size_t)8 * L.fw * sizeof(uint32_t));
     L.off_longq = o; o = align16(o + (size_t)spc * sizeof(int32_t));
     L.off_smap = o; o = align16(o + (size_t)wpc * 8 * 2 * sizeof(StageMap));
     L.off_hist = o; o = align16(o + (size_t)NWARP * 2 * HB * sizeof(int32_t));
-    L.off_walk = o; o = align16(o + (size_t)8 * 32 * NT);
+    L.off_walk = o; o = align16(o + (size_t)8 * P * sizeof(uint4));
     L.off_row = o; o = align16(o + (size_t)(max_row + 4) * sizeof(uint32_t));
     L.off_misc = o; o = align16(o + 64 * sizeof(int64_t));
     L.total = o;
@@ -874,22 +878,22 @@ __host__ __device__ inline SortedLayout sorted_layout(int spc, int wpc, int max_
 }
 
 // chain buffers carved from the scratch table area: exact outgoing G [P][8] (epoch << 32 | G),
-// table-ready flags [P], byte tables [P][8][64]
+// table-ready flags [P], block staircases [P][8] (16 bytes each)
 __host__ __device__ inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 __host__ __device__ inline size_t chain_off_flag(int P) { return align256((size_t)P * 8 * sizeof(uint64_t)); }
 __host__ __device__ inline size_t chain_off_tab(int P) { return chain_off_flag(P) + align256((size_t)P * sizeof(uint32_t)); }
-__host__ __device__ inline size_t chain_bytes(int P) { return chain_off_tab(P) + (size_t)P * 8 * NT; }
+__host__ __device__ inline size_t chain_bytes(int P) { return chain_off_tab(P) + (size_t)P * 8 * sizeof(uint4); }
 
-__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t *p)
-{
-    uint32_t v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
 __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p)
 {
     unsigned long long v;
     asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t *p)
+{
+    uint32_t v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
 __device__ __forceinline__ void st_release_u32(uint32_t *p, uint32_t v)
@@ -901,18 +905,8 @@ __device__ __forceinline__ void st_release_u64(unsigned long long *p, unsigned l
     asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-// bounded waits: false (error word set) after SPIN_LIMIT polls or when another block failed
-__device__ __forceinline__ bool wait_flag(const uint32_t *f, uint32_t want, const GdiGridScratch &X)
-{
-    long long spins = 0;
-    while (ld_acquire_u32(f) != want) {
-        if (++spins > SPIN_LIMIT) { atomicExch(X.err, GDI_DEVERR_TIMEOUT); return false; }
-        if ((spins & 63) == 0 && *(volatile int *)X.err) return false;
-        __nanosleep(32);
-    }
-    return true;
-}
-
+// bounded wait for an exact G word of this epoch: false (error word set) after SPIN_LIMIT polls
+// or when another block failed
 __device__ __forceinline__ bool wait_exact(const unsigned long long *f, uint32_t epoch, const GdiGridScratch &X,
                                            int32_t &g)
 {
@@ -1034,6 +1028,39 @@ __device__ __forceinline__ int stage_apply(const StageMap &m, int t)
     return (y >= 0 && y < NT) ? y : -1;
 }
 
+// Block staircase from the composed table T (lane l holds T[l] in t0 and T[l + 32] in t1; -1 =
+// off the lattice): {rise mask lo, rise mask hi, ylo | lo << 16 | hi << 24, 0}, where the inputs
+// [lo, hi] stay on the lattice and T[j] = ylo + popcount(mask & bits below j) there.
+__device__ __forceinline__ uint4 staircase_of(int t0, int t1)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned v0 = __ballot_sync(0xFFFFFFFFu, t0 >= 0), v1 = __ballot_sync(0xFFFFFFFFu, t1 >= 0);
+    const int n0 = __shfl_down_sync(0xFFFFFFFFu, t0, 1);
+    const int n1 = __shfl_down_sync(0xFFFFFFFFu, t1, 1);
+    const int t32 = __shfl_sync(0xFFFFFFFFu, t1, 0);
+    const int nx0 = lane < 31 ? n0 : t32;
+    const unsigned r0 = __ballot_sync(0xFFFFFFFFu, t0 >= 0 && nx0 > t0);
+    const unsigned r1 = __ballot_sync(0xFFFFFFFFu, lane < 31 && t1 >= 0 && n1 > t1);
+    const unsigned long long V = ((unsigned long long)v1 << 32) | v0;
+    int lo = NT, hi = -1, ylo = 0;
+    if (V) {
+        lo = __ffsll((long long)V) - 1;
+        hi = 63 - __clzll((long long)V);
+    }
+    const int yv = __shfl_sync(0xFFFFFFFFu, lo < 32 ? t0 : t1, lo & 31);
+    if (V) ylo = yv;
+    return make_uint4(r0, r1, ((uint32_t)ylo & 0xFFFFu) | ((uint32_t)lo << 16) | ((uint32_t)(hi & 0xFF) << 24), 0u);
+}
+
+__device__ __forceinline__ int staircase_eval(const uint4 &e, int idx)
+{
+    const int lo = (int)((e.z >> 16) & 0xFFu);
+    const int hi = (int)(int8_t)(uint8_t)(e.z >> 24);
+    if (idx < lo || idx > hi) return -1;
+    const unsigned long long m = ((unsigned long long)e.y << 32) | e.x;
+    return (int)(int16_t)(uint16_t)(e.z & 0xFFFFu) + __popcll(m & ((1ull << idx) - 1ull));
+}
+
 __global__ void __launch_bounds__(GB, 1) gdi_grid_sorted_kernel(GridArgs A)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1043,14 +1070,15 @@ __global__ void __launch_bounds__(GB, 1) gdi_grid_sorted_kernel(GridArgs A)
     const int Pb = gridDim.x, p = blockIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int spc = A.spc;
-    const SortedLayout L = sorted_layout(spc, A.wpc, R.max_row);
+    const SortedLayout L = sorted_layout(spc, A.wpc, R.max_row, Pb);
     int16_t *hb = reinterpret_cast<int16_t *>(smem_raw + L.off_h);   // fields [i*8 + r], then rel [r*spc + i]
     int32_t *gam = reinterpret_cast<int32_t *>(smem_raw + L.off_gam);
     uint8_t *s0 = smem_raw + L.off_s0;
     uint32_t *fm = reinterpret_cast<uint32_t *>(smem_raw + L.off_fm);
     StageMap *smap = reinterpret_cast<StageMap *>(smem_raw + L.off_smap);
     int32_t *hist = reinterpret_cast<int32_t *>(smem_raw + L.off_hist);
-    int8_t *walk = reinterpret_cast<int8_t *>(smem_raw + L.off_walk);
+    uint4 *walk = reinterpret_cast<uint4 *>(smem_raw + L.off_walk);
+    uint32_t *fbits = reinterpret_cast<uint32_t *>(smem_raw + L.off_fbits);   // [r][fw] fast-path flips
     GSmem S = {};
     S.longq = reinterpret_cast<int32_t *>(smem_raw + L.off_longq);
     S.hist = hist;
@@ -1060,7 +1088,7 @@ __global__ void __launch_bounds__(GB, 1) gdi_grid_sorted_kernel(GridArgs A)
     unsigned char *cb = reinterpret_cast<unsigned char *>(X.tables);
     unsigned long long *exg = reinterpret_cast<unsigned long long *>(cb);
     uint32_t *flag = reinterpret_cast<uint32_t *>(cb + chain_off_flag(Pb));
-    int8_t *tabs = reinterpret_cast<int8_t *>(cb + chain_off_tab(Pb));
+    uint4 *tabs = reinterpret_cast<uint4 *>(cb + chain_off_tab(Pb));
     const int64_t base = P.node_off[0];
     const int32_t n = (int32_t)(P.node_off[1] - base);
     const int32_t *cls = P.class_ptr + P.class_off[0];
@@ -1103,6 +1131,7 @@ __global__ void __launch_bounds__(GB, 1) gdi_grid_sorted_kernel(GridArgs A)
                 else window_maps<8>(gr, s0, rr, ws, wlen, r, Gc[r], o);
             }
             for (int i = threadIdx.x; i < (ns + 3) / 4; i += GB) fm[i] = 0;
+            for (int i = threadIdx.x; i < 8 * L.fw; i += GB) fbits[i] = 0;
             __syncthreads();
             // ---- block table per replica: lanes hold lattice points lane and lane + 32
             int t0 = lane, t1 = lane + 32;
@@ -1116,9 +1145,8 @@ __global__ void __launch_bounds__(GB, 1) gdi_grid_sorted_kernel(GridArgs A)
                         t1 = stage_apply(m, t1);
                     }
                 }
-                int8_t *dst = tabs + ((size_t)p * 8 + r) * NT;
-                dst[lane] = (int8_t)t0;
-                dst[lane + 32] = (int8_t)t1;
+                const uint4 st = staircase_of(t0, t1);
+                if (lane == 0) tabs[(size_t)p * 8 + r] = st;
                 __threadfence();
             }
             __syncthreads();
@@ -1127,46 +1155,60 @@ __global__ void __launch_bounds__(GB, 1) gdi_grid_sorted_kernel(GridArgs A)
             if (warp < nrep) {
                 const int r = warp;
                 const int32_t c0 = Gc[r];
-                int8_t *wb = walk + (size_t)r * 32 * NT;
-                int idx = NT / 2;          // lattice index of the running G, or -1 when off the lattice
-                int32_t gx = c0;           // the running G when off the lattice
+                uint4 *wb = walk + (size_t)r * Pb;
                 bool ok = true;
-                for (int j0 = 0; j0 < p && ok; j0 += 32) {
-                    const int j = j0 + lane;
-                    bool mine = true;
-                    if (j < p) {
-                        mine = wait_flag(flag + j, epoch, X);
-                        if (mine) {
-                            const uint4 *src = reinterpret_cast<const uint4 *>(tabs + ((size_t)j * 8 + r) * NT);
-                            const uint4 v0 = __ldcg(src), v1 = __ldcg(src + 1), v2 = __ldcg(src + 2),
-                                        v3 = __ldcg(src + 3);
-                            uint4 *d4 = reinterpret_cast<uint4 *>(wb + (size_t)lane * NT);
-                            d4[0] = v0;
-                            d4[1] = v1;
-                            d4[2] = v2;
-                            d4[3] = v3;
-                        }
+                {
+                    // every lane polls the flags of blocks lane, lane + 32, ... (relaxed loads, all in
+                    // flight together); one fence once all are seen, then the entries are fetched
+                    unsigned pend = 0;
+                    for (int m = 0; lane + 32 * m < p; ++m) pend |= 1u << m;
+                    const unsigned want = pend;
+                    long long spins = 0;
+                    while (pend) {
+                        unsigned seen = 0;
+                        for (int m = 0; m < 32; ++m)
+                            if ((pend >> m) & 1u)
+                                if (ld_relaxed_u32(flag + lane + 32 * m) == epoch) seen |= 1u << m;
+                        pend &= ~seen;
+                        if (!pend) break;
+                        if (++spins > SPIN_LIMIT) { atomicExch(X.err, GDI_DEVERR_TIMEOUT); ok = false; break; }
+                        if ((spins & 63) == 0 && *(volatile int *)X.err) { ok = false; break; }
+                        __nanosleep(20);
                     }
-                    ok = __all_sync(0xFFFFFFFFu, mine);
-                    __syncwarp();
-                    if (!ok) break;
-                    const int nb = min(32, p - j0);
-                    for (int l = 0; l < nb && ok; ++l) {
-                        const int nidx = idx >= 0 ? (int)wb[l * NT + idx] : -1;
-                        if (nidx >= 0) { idx = nidx; continue; }
-                        int32_t v = 0;
-                        ok = wait_exact(exg + (size_t)(j0 + l) * 8 + r, epoch, X, v);
-                        gx = v;
-                        const int32_t xr = gx - c0;
-                        idx = (xr >= -NT && xr <= NT - 2) ? (xr + NT) >> 1 : -1;
-                    }
+                    __threadfence();
+                    for (int m = 0; m < 32; ++m)
+                        if ((want >> m) & 1u) wb[lane + 32 * m] = __ldcg(tabs + (size_t)(lane + 32 * m) * 8 + r);
                     ok = __all_sync(0xFFFFFFFFu, ok);
                     __syncwarp();
                 }
+                int idx = NT / 2;          // lattice index of the running G, or -1 when off the lattice
+                int32_t gx = c0;           // the running G when off the lattice
+                int j = 0;
+                while (ok && j < p) {
+                    // staircase steps while the running G stays on the lattice
+                    if (idx >= 0) {
+#pragma unroll 8
+                        for (; j < p; ++j) {
+                            const int nidx = staircase_eval(wb[j], idx);
+                            if (nidx < 0) break;
+                            idx = nidx;
+                        }
+                        if (j >= p) break;
+                    }
+                    // block j cannot map the running G: it publishes its exact outgoing G
+                    int32_t v = 0;
+                    ok = wait_exact(exg + (size_t)j * 8 + r, epoch, X, v);
+                    gx = v;
+                    const int32_t xr = gx - c0;
+                    idx = (xr >= -NT && xr <= NT - 2) ? (xr + NT) >> 1 : -1;
+                    ++j;
+                }
+                ok = __all_sync(0xFFFFFFFFu, ok);
                 if (ok) {
                     const int32_t gin = idx >= 0 ? c0 - NT + 2 * idx : gx;
                     const int own = __shfl_sync(0xFFFFFFFFu, (idx >= 0 && idx < 32) ? t0 : t1, idx & 31);
                     const bool need_exact = idx < 0 || own < 0;
+                    uint32_t *fb = fbits + (size_t)r * L.fw;
                     int32_t x = gin - c0;
                     const int32_t *gr = gam + (size_t)r * spc;
                     const int16_t *rr = hb + (size_t)r * spc;
@@ -1178,17 +1220,24 @@ __global__ void __launch_bounds__(GB, 1) gdi_grid_sorted_kernel(GridArgs A)
                             for (int ph = 0; ph < 2; ++ph) {
                                 const bool plus = plus_first == (ph == 0);
                                 int32_t cnt = 0;
-                                for (int i = ws + lane; i < we; i += 32) {
-                                    const bool neg = (s0[i] >> r) & 1;
-                                    if (neg != plus) {
-                                        const int32_t rv = rr[i];
-                                        if (plus ? rv <= x : rv >= x) {
-                                            ++cnt;
-                                            atomicOr(&fm[i >> 2], 1u << (8 * (i & 3) + r));
+                                for (int q = ws; q < we; q += 32) {
+                                    const int i = q + lane;
+                                    bool f = false;
+                                    if (i < we) {
+                                        const bool neg = (s0[i] >> r) & 1;
+                                        if (neg != plus) {
+                                            const int32_t rv = rr[i];
+                                            f = plus ? rv <= x : rv >= x;
                                         }
                                     }
+                                    const unsigned bm = __ballot_sync(0xFFFFFFFFu, f);
+                                    cnt += __popc(bm);
+                                    if (lane == 0 && bm) {
+                                        const int sh = q & 31;
+                                        fb[q >> 5] |= bm << sh;
+                                        if (sh) fb[(q >> 5) + 1] |= bm >> (32 - sh);
+                                    }
                                 }
-                                cnt = __reduce_add_sync(0xFFFFFFFFu, cnt);
                                 x = plus ? x - 2 * cnt : x + 2 * cnt;
                             }
                         } else {
@@ -1213,8 +1262,9 @@ __global__ void __launch_bounds__(GB, 1) gdi_grid_sorted_kernel(GridArgs A)
             }
             __syncthreads();
             for (int32_t i = threadIdx.x; i < ns; i += GB) {
-                const uint8_t f = (uint8_t)(fm[i >> 2] >> (8 * (i & 3)));
-                if (f) X.packed[base + a0 + i] = s0[i] ^ f;
+                uint32_t f = (fm[i >> 2] >> (8 * (i & 3))) & 0xFFu;
+                for (int r = 0; r < nrep; ++r) f |= ((fbits[(size_t)r * L.fw + (i >> 5)] >> (i & 31)) & 1u) << r;
+                if (f) X.packed[base + a0 + i] = (uint8_t)(s0[i] ^ f);
             }
             if (!grid_sync(X)) return;
         }
@@ -1420,7 +1470,7 @@ int gdi_grid_plan(const GdiDevProblem &P, int max_row, int sms, int *spc, int *w
     // long rows keep their chunk counts in the histogram area
     if ((size_t)*spc > (size_t)NWARP * 2 * HB) return -1;
     if (P.W <= SMAXW) {
-        *smem = sorted_layout(*spc, *wpc, max_row).total;
+        *smem = sorted_layout(*spc, *wpc, max_row, sms).total;
         return 0;
     }
     // the exact chain fallback of the tabulated path keeps thresholds, fields, start signs and bins
