@@ -831,11 +831,12 @@ __global__ void __launch_bounds__(GB, 1) gdi_grid_anneal_kernel(GridArgs A)
 //
 // Block maps: on the lattice x = G - c in {-64, -62, ..., 62} (64 points; G - c is always even) a
 // group is a staircase: index j -> ylo + popcount(mask & bits below j), read from where the a_k
-// (b_k) fall.  The maps of a block's windows are composed per replica (64 lattice points, two per
-// lane); the composition is again a staircase on the interval of inputs that stay on the lattice,
-// published as 16 bytes (rise mask, value at the interval start, interval) with a release flag.
-// Every block then fetches the entries of the blocks before it (acquire loads, all at once) and
-// walks them from c to its exact entering G without a grid barrier.  Where the walk leaves the lattice, the block whose table failed publishes its exact
+// (b_k) fall.  The maps of a block's windows are composed per replica into a 64-entry byte table
+// (two lattice points per lane; -1 = leaves the lattice) and published with a release flag.  The
+// last block of every run of 16 blocks also composes the run's tables into a run table.  Every
+// block then fetches the run tables before it and the block tables of its own run (flag polls,
+// one fence, all fetches at once) and looks its exact entering G up from c: at most
+// 160 / 16 + 15 byte lookups, without a grid barrier.  Where the walk leaves the lattice, the block whose table failed publishes its exact
 // outgoing G (it knows its own entering G and replays exactly), and the walk continues from it.
 // One grid barrier per class remains: the next class reads this class's spins.
 constexpr int SMAXW = 256;
@@ -844,6 +845,10 @@ constexpr int32_t KEY_D = 1 << 22;      // threshold distances are clamped to [-
 constexpr int32_t REL_CAP = 32767;      // rel values are stored clamped to +-REL_CAP
 constexpr int32_t FAST_X = 32000;       // |G - c| up to which the stored rel values decide exactly
 constexpr unsigned long long STEP_MASK = (1ull << (NT - 1)) - 1ull;
+constexpr int RUN = 16;                 // blocks per run table
+__host__ __device__ inline int nruns(int P) { return (P + RUN - 1) / RUN; }
+// per replica warp: run tables [nruns] + own-run block tables [RUN] + descent tables [RUN]
+__host__ __device__ inline int walk_slots(int P) { return nruns(P) + 2 * RUN; }
 
 struct StageMap {
     unsigned long long mask;            // bit j: the step from lattice point j to j + 1 rises
@@ -870,7 +875,7 @@ __host__ __device__ inline SortedLayout sorted_layout(int spc, int wpc, int max_
     L.off_longq = o; o = align16(o + (size_t)spc * sizeof(int32_t));
     L.off_smap = o; o = align16(o + (size_t)wpc * 8 * 2 * sizeof(StageMap));
     L.off_hist = o; o = align16(o + (size_t)NWARP * 2 * HB * sizeof(int32_t));
-    L.off_walk = o; o = align16(o + (size_t)8 * P * sizeof(uint4));
+    L.off_walk = o; o = align16(o + (size_t)8 * walk_slots(P) * NT);
     L.off_row = o; o = align16(o + (size_t)(max_row + 4) * sizeof(uint32_t));
     L.off_misc = o; o = align16(o + 64 * sizeof(int64_t));
     L.total = o;
@@ -878,11 +883,13 @@ __host__ __device__ inline SortedLayout sorted_layout(int spc, int wpc, int max_
 }
 
 // chain buffers carved from the scratch table area: exact outgoing G [P][8] (epoch << 32 | G),
-// table-ready flags [P], block staircases [P][8] (16 bytes each)
+// block-table flags [P], run-table flags [NR], block tables [P][8][64], run tables [NR][8][64]
 __host__ __device__ inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 __host__ __device__ inline size_t chain_off_flag(int P) { return align256((size_t)P * 8 * sizeof(uint64_t)); }
-__host__ __device__ inline size_t chain_off_tab(int P) { return chain_off_flag(P) + align256((size_t)P * sizeof(uint32_t)); }
-__host__ __device__ inline size_t chain_bytes(int P) { return chain_off_tab(P) + (size_t)P * 8 * sizeof(uint4); }
+__host__ __device__ inline size_t chain_off_rflag(int P) { return chain_off_flag(P) + align256((size_t)P * sizeof(uint32_t)); }
+__host__ __device__ inline size_t chain_off_tab(int P) { return chain_off_rflag(P) + align256((size_t)nruns(P) * sizeof(uint32_t)); }
+__host__ __device__ inline size_t chain_off_rtab(int P) { return chain_off_tab(P) + (size_t)P * 8 * NT; }
+__host__ __device__ inline size_t chain_bytes(int P) { return chain_off_rtab(P) + (size_t)nruns(P) * 8 * NT; }
 
 __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p)
 {
@@ -1028,37 +1035,38 @@ __device__ __forceinline__ int stage_apply(const StageMap &m, int t)
     return (y >= 0 && y < NT) ? y : -1;
 }
 
-// Block staircase from the composed table T (lane l holds T[l] in t0 and T[l + 32] in t1; -1 =
-// off the lattice): {rise mask lo, rise mask hi, ylo | lo << 16 | hi << 24, 0}, where the inputs
-// [lo, hi] stay on the lattice and T[j] = ylo + popcount(mask & bits below j) there.
-__device__ __forceinline__ uint4 staircase_of(int t0, int t1)
+// warp: fetch the byte tables of `cnt` entries (src + k * stride, k < cnt <= 32) into dst[k][64]
+__device__ __forceinline__ void fetch_tables(const int8_t *src, size_t stride, int cnt, int8_t *dst)
 {
     const int lane = threadIdx.x & 31;
-    const unsigned v0 = __ballot_sync(0xFFFFFFFFu, t0 >= 0), v1 = __ballot_sync(0xFFFFFFFFu, t1 >= 0);
-    const int n0 = __shfl_down_sync(0xFFFFFFFFu, t0, 1);
-    const int n1 = __shfl_down_sync(0xFFFFFFFFu, t1, 1);
-    const int t32 = __shfl_sync(0xFFFFFFFFu, t1, 0);
-    const int nx0 = lane < 31 ? n0 : t32;
-    const unsigned r0 = __ballot_sync(0xFFFFFFFFu, t0 >= 0 && nx0 > t0);
-    const unsigned r1 = __ballot_sync(0xFFFFFFFFu, lane < 31 && t1 >= 0 && n1 > t1);
-    const unsigned long long V = ((unsigned long long)v1 << 32) | v0;
-    int lo = NT, hi = -1, ylo = 0;
-    if (V) {
-        lo = __ffsll((long long)V) - 1;
-        hi = 63 - __clzll((long long)V);
+    if (lane < cnt) {
+        const uint4 *s4 = reinterpret_cast<const uint4 *>(src + (size_t)lane * stride);
+        const uint4 v0 = __ldcg(s4), v1 = __ldcg(s4 + 1), v2 = __ldcg(s4 + 2), v3 = __ldcg(s4 + 3);
+        uint4 *d4 = reinterpret_cast<uint4 *>(dst + (size_t)lane * NT);
+        d4[0] = v0;
+        d4[1] = v1;
+        d4[2] = v2;
+        d4[3] = v3;
     }
-    const int yv = __shfl_sync(0xFFFFFFFFu, lo < 32 ? t0 : t1, lo & 31);
-    if (V) ylo = yv;
-    return make_uint4(r0, r1, ((uint32_t)ylo & 0xFFFFu) | ((uint32_t)lo << 16) | ((uint32_t)(hi & 0xFF) << 24), 0u);
+    __syncwarp();
 }
 
-__device__ __forceinline__ int staircase_eval(const uint4 &e, int idx)
+// warp: bounded poll until every flag f[k * 1], k < cnt <= 32, holds `want` (relaxed loads, then one
+// fence).  Returns false (error word set) on timeout or when another block failed.
+__device__ __forceinline__ bool poll_flags(const uint32_t *f, int cnt, uint32_t want, const GdiGridScratch &X)
 {
-    const int lo = (int)((e.z >> 16) & 0xFFu);
-    const int hi = (int)(int8_t)(uint8_t)(e.z >> 24);
-    if (idx < lo || idx > hi) return -1;
-    const unsigned long long m = ((unsigned long long)e.y << 32) | e.x;
-    return (int)(int16_t)(uint16_t)(e.z & 0xFFFFu) + __popcll(m & ((1ull << idx) - 1ull));
+    const int lane = threadIdx.x & 31;
+    bool ok = true;
+    if (lane < cnt) {
+        long long spins = 0;
+        while (ld_relaxed_u32(f + lane) != want) {
+            if (++spins > SPIN_LIMIT) { atomicExch(X.err, GDI_DEVERR_TIMEOUT); ok = false; break; }
+            if ((spins & 63) == 0 && *(volatile int *)X.err) { ok = false; break; }
+            __nanosleep(20);
+        }
+    }
+    __threadfence();
+    return __all_sync(0xFFFFFFFFu, ok);
 }
 
 __global__ void __launch_bounds__(GB, 1) gdi_grid_sorted_kernel(GridArgs A)
@@ -1077,7 +1085,7 @@ __global__ void __launch_bounds__(GB, 1) gdi_grid_sorted_kernel(GridArgs A)
     uint32_t *fm = reinterpret_cast<uint32_t *>(smem_raw + L.off_fm);
     StageMap *smap = reinterpret_cast<StageMap *>(smem_raw + L.off_smap);
     int32_t *hist = reinterpret_cast<int32_t *>(smem_raw + L.off_hist);
-    uint4 *walk = reinterpret_cast<uint4 *>(smem_raw + L.off_walk);
+    int8_t *walk = reinterpret_cast<int8_t *>(smem_raw + L.off_walk);
     uint32_t *fbits = reinterpret_cast<uint32_t *>(smem_raw + L.off_fbits);   // [r][fw] fast-path flips
     GSmem S = {};
     S.longq = reinterpret_cast<int32_t *>(smem_raw + L.off_longq);
@@ -1088,7 +1096,12 @@ __global__ void __launch_bounds__(GB, 1) gdi_grid_sorted_kernel(GridArgs A)
     unsigned char *cb = reinterpret_cast<unsigned char *>(X.tables);
     unsigned long long *exg = reinterpret_cast<unsigned long long *>(cb);
     uint32_t *flag = reinterpret_cast<uint32_t *>(cb + chain_off_flag(Pb));
-    uint4 *tabs = reinterpret_cast<uint4 *>(cb + chain_off_tab(Pb));
+    uint32_t *rflag = reinterpret_cast<uint32_t *>(cb + chain_off_rflag(Pb));
+    int8_t *tabs = reinterpret_cast<int8_t *>(cb + chain_off_tab(Pb));
+    int8_t *rtabs = reinterpret_cast<int8_t *>(cb + chain_off_rtab(Pb));
+    const int NR = nruns(Pb);
+    const int run = p / RUN, run0 = run * RUN;
+    const bool leader = (p % RUN == RUN - 1) || p == Pb - 1;
     const int64_t base = P.node_off[0];
     const int32_t n = (int32_t)(P.node_off[1] - base);
     const int32_t *cls = P.class_ptr + P.class_off[0];
@@ -1145,64 +1158,79 @@ __global__ void __launch_bounds__(GB, 1) gdi_grid_sorted_kernel(GridArgs A)
                         t1 = stage_apply(m, t1);
                     }
                 }
-                const uint4 st = staircase_of(t0, t1);
-                if (lane == 0) tabs[(size_t)p * 8 + r] = st;
+                int8_t *dst = tabs + ((size_t)p * 8 + r) * NT;
+                dst[lane] = (int8_t)t0;
+                dst[lane + 32] = (int8_t)t1;
                 __threadfence();
             }
             __syncthreads();
             if (threadIdx.x == 0) st_release_u32(flag + p, epoch);
-            // ---- entering G: walk the tables of blocks 0 .. p-1 from c; then the exact replay
+            // ---- the last block of a run composes the run's block tables into the run table
+            bool ok = true;
+            if (leader) {
+                if (warp < nrep) {
+                    const int r = warp;
+                    int8_t *dt = walk + ((size_t)r * walk_slots(Pb) + NR + RUN) * NT;   // descent slots
+                    const int cnt = p - run0;                 // blocks of the run before me
+                    ok = poll_flags(flag + run0, cnt, epoch, X);
+                    if (ok) {
+                        fetch_tables(tabs + ((size_t)run0 * 8 + r) * NT, (size_t)8 * NT, cnt, dt);
+                        int u0 = lane, u1 = lane + 32;
+                        for (int k = 0; k < cnt; ++k) {
+                            if (u0 >= 0) u0 = dt[k * NT + u0];
+                            if (u1 >= 0) u1 = dt[k * NT + u1];
+                        }
+                        // then my own table (lane l holds T[l], T[l + 32])
+                        const int x00 = __shfl_sync(0xFFFFFFFFu, t0, u0 & 31);
+                        const int x01 = __shfl_sync(0xFFFFFFFFu, t1, u0 & 31);
+                        const int x10 = __shfl_sync(0xFFFFFFFFu, t0, u1 & 31);
+                        const int x11 = __shfl_sync(0xFFFFFFFFu, t1, u1 & 31);
+                        u0 = u0 < 0 ? -1 : (u0 >= 32 ? x01 : x00);
+                        u1 = u1 < 0 ? -1 : (u1 >= 32 ? x11 : x10);
+                        int8_t *rd = rtabs + ((size_t)run * 8 + r) * NT;
+                        rd[lane] = (int8_t)u0;
+                        rd[lane + 32] = (int8_t)u1;
+                        __threadfence();
+                    }
+                }
+                __syncthreads();
+                if (threadIdx.x == 0) st_release_u32(rflag + run, epoch);
+            }
+            // ---- entering G: run tables of the runs before mine, then the block tables of my run
             if (warp < nrep) {
                 const int r = warp;
                 const int32_t c0 = Gc[r];
-                uint4 *wb = walk + (size_t)r * Pb;
-                bool ok = true;
-                {
-                    // every lane polls the flags of blocks lane, lane + 32, ... (relaxed loads, all in
-                    // flight together); one fence once all are seen, then the entries are fetched
-                    unsigned pend = 0;
-                    for (int m = 0; lane + 32 * m < p; ++m) pend |= 1u << m;
-                    const unsigned want = pend;
-                    long long spins = 0;
-                    while (pend) {
-                        unsigned seen = 0;
-                        for (int m = 0; m < 32; ++m)
-                            if ((pend >> m) & 1u)
-                                if (ld_relaxed_u32(flag + lane + 32 * m) == epoch) seen |= 1u << m;
-                        pend &= ~seen;
-                        if (!pend) break;
-                        if (++spins > SPIN_LIMIT) { atomicExch(X.err, GDI_DEVERR_TIMEOUT); ok = false; break; }
-                        if ((spins & 63) == 0 && *(volatile int *)X.err) { ok = false; break; }
-                        __nanosleep(20);
-                    }
-                    __threadfence();
-                    for (int m = 0; m < 32; ++m)
-                        if ((want >> m) & 1u) wb[lane + 32 * m] = __ldcg(tabs + (size_t)(lane + 32 * m) * 8 + r);
-                    ok = __all_sync(0xFFFFFFFFu, ok);
-                    __syncwarp();
+                int8_t *ws_run = walk + (size_t)r * walk_slots(Pb) * NT;    // [NR][64]
+                int8_t *ws_own = ws_run + (size_t)NR * NT;                   // [RUN][64]
+                int8_t *ws_dsc = ws_own + (size_t)RUN * NT;                  // [RUN][64]
+                const int nown = p - run0;
+                if (ok) ok = poll_flags(rflag, run, epoch, X);
+                if (ok) ok = poll_flags(flag + run0, nown, epoch, X);
+                if (ok) {
+                    fetch_tables(rtabs + (size_t)r * NT, (size_t)8 * NT, run, ws_run);
+                    fetch_tables(tabs + ((size_t)run0 * 8 + r) * NT, (size_t)8 * NT, nown, ws_own);
                 }
                 int idx = NT / 2;          // lattice index of the running G, or -1 when off the lattice
                 int32_t gx = c0;           // the running G when off the lattice
-                int j = 0;
-                while (ok && j < p) {
-                    // staircase steps while the running G stays on the lattice
-                    if (idx >= 0) {
-#pragma unroll 8
-                        for (; j < p; ++j) {
-                            const int nidx = staircase_eval(wb[j], idx);
-                            if (nidx < 0) break;
-                            idx = nidx;
-                        }
-                        if (j >= p) break;
-                    }
-                    // block j cannot map the running G: it publishes its exact outgoing G
+                // one block step: its table, or its exact outgoing G where the table cannot map
+                auto block_step = [&](const int8_t *t, int j) {
+                    const int nidx = idx >= 0 ? (int)t[idx] : -1;
+                    if (nidx >= 0) { idx = nidx; return; }
                     int32_t v = 0;
                     ok = wait_exact(exg + (size_t)j * 8 + r, epoch, X, v);
                     gx = v;
                     const int32_t xr = gx - c0;
                     idx = (xr >= -NT && xr <= NT - 2) ? (xr + NT) >> 1 : -1;
-                    ++j;
+                };
+                for (int q = 0; q < run && ok; ++q) {
+                    const int nidx = idx >= 0 ? (int)ws_run[q * NT + idx] : -1;
+                    if (nidx >= 0) { idx = nidx; continue; }
+                    // the run table cannot map the running G: walk the run block by block
+                    fetch_tables(tabs + ((size_t)q * RUN * 8 + r) * NT, (size_t)8 * NT, RUN, ws_dsc);
+                    for (int k = 0; k < RUN && ok; ++k) block_step(ws_dsc + k * NT, q * RUN + k);
+                    __syncwarp();
                 }
+                for (int k = 0; k < nown && ok; ++k) block_step(ws_own + k * NT, run0 + k);
                 ok = __all_sync(0xFFFFFFFFu, ok);
                 if (ok) {
                     const int32_t gin = idx >= 0 ? c0 - NT + 2 * idx : gx;
