@@ -79,6 +79,11 @@ struct gdi_ctx {
     DevBuf<int32_t> g_gin, g_Gcls, g_err, g_status, g_rhist, g_rties, g_rparams;
     DevBuf<unsigned int> g_bar;
     bool used_grid = false;
+    // cost-weighted split of every colour class over the grid path's blocks: window costs (one
+    // instance, W >= 1), and the device copy of the bounds for the last block count and cap
+    std::vector<int64_t> wcost, wcost_off;
+    DevBuf<int32_t> g_wbnd;
+    int wbnd_blocks = 0, wbnd_wpc = 0;
     std::vector<int32_t> num_classes;       // per instance
     DevBuf<int64_t> node_off, row_ptr;
     DevBuf<int32_t> class_off, class_ptr, rank_of;
@@ -136,6 +141,7 @@ struct gdi_ctx {
         tab.release(); tab_off.release(); temp.release(); raw_G.release(); final_G.release(); tr_G.release();
         err.release(); raw_cut.release(); final_cut.release(); tr_cut.release(); tr_digest.release();
         g_packed.release(); g_rflags.release(); g_tables.release(); g_gin.release(); g_Gcls.release();
+        g_wbnd.release();
         g_err.release(); g_status.release(); g_rhist.release(); g_rties.release(); g_rparams.release();
         g_bar.release();
         item_order.release(); item_counter.release();
@@ -429,6 +435,20 @@ int gdi_create(gdi_ctx **out, const gdi_graph *g, const gdi_model *m)
         }
         rp[(size_t)N] = e_out;
     }
+    // window costs for the grid path's weighted split: a rank costs its degree plus a constant for
+    // its threshold and its share of the window sort (both measured as about 12 neighbour reads)
+    if (Q == 1 && c->W >= 1) {
+        const int32_t nclass = c->num_classes[0];
+        c->wcost_off.assign((size_t)nclass + 1, 0);
+        for (int32_t k = 0; k < nclass; ++k) {
+            const int32_t c0 = class_ptr[(size_t)k], c1 = class_ptr[(size_t)k + 1];
+            for (int32_t a = c0; a < c1; a += c->W) {
+                const int32_t b = std::min(a + c->W, c1);
+                c->wcost.push_back((rp[(size_t)b] - rp[(size_t)a]) + (int64_t)12 * (b - a));
+            }
+            c->wcost_off[(size_t)k + 1] = (int64_t)c->wcost.size();
+        }
+    }
 
     cudaError_t e;
 #define GDI_UP(buf, vec)                                                                          \
@@ -629,7 +649,7 @@ int gdi_anneal(gdi_ctx *c, const gdi_schedule *S, const gdi_run *run)
         int spc = 0, wpc = 0;
         size_t smem = 0;
         const int nblk = c->grid_limit > 0 ? std::min(c->grid_limit, sms) : sms;
-        if (gdi_grid_plan(P, max_row, nblk, &spc, &wpc, &smem) != 0 || smem > (size_t)max_optin)
+        if (gdi_grid_plan(P, max_row, nblk, (size_t)max_optin, &spc, &wpc, &smem) != 0)
             return fail(GDI_ERR_TOO_LARGE, "grid-scale plan needs " + std::to_string(smem) +
                                                " bytes of shared memory per block; use a smaller W");
         const int D = c->max_degree;
@@ -648,7 +668,22 @@ int gdi_anneal(gdi_ctx *c, const gdi_schedule *S, const gdi_run *run)
         cudaMemsetAsync(c->g_err.p, 0, sizeof(int32_t), st);
         cudaMemsetAsync(c->g_status.p, 0, 16 * sizeof(int32_t), st);
         const GdiGridScratch X = c->grid_scratch();
-        int ke = gdi_launch_grid_anneal(P, R, X, c->spins.p, nblk, spc, wpc, smem, st);
+        const int32_t *wbnd = nullptr;
+        if (c->W <= 256 && !c->wcost_off.empty()) {
+            if (c->wbnd_blocks != nblk || c->wbnd_wpc != wpc) {
+                const int ncls = (int)c->wcost_off.size() - 1;
+                std::vector<int32_t> bnd((size_t)ncls * (nblk + 1));
+                gdi_grid_window_bounds(c->wcost.data(), c->wcost_off.data(), ncls, nblk, wpc, bnd.data());
+                e = c->g_wbnd.alloc(bnd.size());
+                if (e == cudaSuccess) e = cudaMemcpy(c->g_wbnd.p, bnd.data(), bnd.size() * sizeof(int32_t),
+                                                     cudaMemcpyHostToDevice);
+                if (e != cudaSuccess) return cuda_fail(e, "window bounds");
+                c->wbnd_blocks = nblk;
+                c->wbnd_wpc = wpc;
+            }
+            wbnd = c->g_wbnd.p;
+        }
+        int ke = gdi_launch_grid_anneal(P, R, X, c->spins.p, nblk, spc, wpc, smem, wbnd, st);
         if (ke) return cuda_fail((cudaError_t)ke, "grid anneal launch");
         ke = gdi_launch_grid_finish(P, R, X, c->spins.p, (run->flags & GDI_FLAG_NO_REPAIR) ? 0 : 1, st);
         if (ke) return cuda_fail((cudaError_t)ke, "grid finish kernels");

@@ -86,6 +86,7 @@ struct GridArgs {
     GdiGridScratch X;
     int rep_base, nrep;
     int spc, wpc;
+    const int32_t *wbnd;    // [classes][blocks + 1] first window of every block, or null (even split)
 };
 
 // ---------------------------------------------------------------------------------------------
@@ -1126,7 +1127,14 @@ __global__ void __launch_bounds__(GB, 1) gdi_grid_sorted_kernel(GridArgs A)
             const int32_t lo = cls[c], hi = cls[c + 1];
             int32_t a0, a1;
             int nwin;
-            class_partition(lo, hi, W, p, Pb, a0, a1, nwin);
+            if (A.wbnd) {
+                const int32_t *bd = A.wbnd + (size_t)c * (Pb + 1);
+                a0 = min(lo + bd[p] * W, hi);
+                a1 = min(lo + bd[p + 1] * W, hi);
+                nwin = bd[p + 1] - bd[p];
+            } else {
+                class_partition(lo, hi, W, p, Pb, a0, a1, nwin);
+            }
             const int32_t ns = a1 - a0;
             if (threadIdx.x < nrep) Gc[threadIdx.x] = *(volatile int32_t *)&X.Gcls[threadIdx.x];
             // ---- thresholds of my ranks (ends with a block barrier)
@@ -1487,10 +1495,11 @@ __global__ void repair_apply_kernel(int8_t *spins, int64_t N, int nrep, const ui
 }  // namespace
 
 // ---------------------------------------------------------------------------------------------
-int gdi_grid_plan(const GdiDevProblem &P, int max_row, int sms, int *spc, int *wpc, size_t *smem)
+int gdi_grid_plan(const GdiDevProblem &P, int max_row, int sms, size_t smem_limit, int *spc, int *wpc,
+                  size_t *smem)
 {
     if (P.num_instances != 1 || P.W < 1) return -1;
-    // windows per block: the largest class decides
+    // windows per block under an even split: the largest class decides
     const int wp = (int)((P.max_class + P.W - 1) / P.W);
     const int w = (wp + sms - 1) / sms;
     *wpc = w < 1 ? 1 : w;
@@ -1498,18 +1507,57 @@ int gdi_grid_plan(const GdiDevProblem &P, int max_row, int sms, int *spc, int *w
     // long rows keep their chunk counts in the histogram area
     if ((size_t)*spc > (size_t)NWARP * 2 * HB) return -1;
     if (P.W <= SMAXW) {
+        // the cost-weighted split stays within the even share of windows per block: more shared
+        // memory per block (less L1) costs more than the finer balance gains
         *smem = sorted_layout(*spc, *wpc, max_row, sms).total;
-        return 0;
+        return *smem <= smem_limit ? 0 : -1;
     }
     // the exact chain fallback of the tabulated path keeps thresholds, fields, start signs and bins
     // of one block's windows (one replica) in the histogram area
     if ((size_t)*spc * 7 + 64 + HA * sizeof(int32_t) > (size_t)NWARP * 2 * HB * sizeof(int32_t)) return -1;
     *smem = grid_layout(*spc, *wpc, sms, max_row).total;
-    return 0;
+    return *smem <= smem_limit ? 0 : -1;
+}
+
+void gdi_grid_window_bounds(const int64_t *cost, const int64_t *cost_off, int num_classes, int blocks,
+                            int wpc, int32_t *bnd)
+{
+    for (int c = 0; c < num_classes; ++c) {
+        const int64_t *w = cost + cost_off[c];
+        const int nw = (int)(cost_off[c + 1] - cost_off[c]);
+        int32_t *K = bnd + (size_t)c * (blocks + 1);
+        int64_t total = 0;
+        for (int k = 0; k < nw; ++k) total += w[k];
+        // ideal cut before block p: the window boundary nearest to p/blocks of the class's cost
+        int k = 0;
+        int64_t pre = 0;
+        K[0] = 0;
+        for (int p = 1; p < blocks; ++p) {
+            const double target = (double)total * p / blocks;
+            while (k < nw && (double)(pre + w[k]) <= target) pre += w[k++];
+            int cut = k;
+            if (k < nw && (double)(pre + w[k]) - target < target - (double)pre) cut = k + 1;
+            K[p] = cut;
+        }
+        K[blocks] = nw;
+        // at most wpc windows per block: clamp to what the blocks before and after can hold
+        for (int p = 0; p <= blocks; ++p) {
+            const int64_t lo = (int64_t)nw - (int64_t)(blocks - p) * wpc;
+            const int64_t hi = (int64_t)p * wpc;
+            int64_t v = K[p];
+            if (v < lo) v = lo;
+            if (v > hi) v = hi;
+            if (p > 0 && v < K[p - 1]) v = K[p - 1];
+            K[p] = (int32_t)v;
+        }
+        for (int p = 0; p < blocks; ++p)
+            if (K[p + 1] > K[p] + wpc) K[p + 1] = K[p] + wpc;
+    }
 }
 
 int gdi_launch_grid_anneal(const GdiDevProblem &P, const GdiDevRun &R, const GdiGridScratch &X,
-                           int8_t *spins, int sms, int spc, int wpc, size_t smem, void *stream)
+                           int8_t *spins, int sms, int spc, int wpc, size_t smem, const int32_t *wbnd,
+                           void *stream)
 {
     cudaStream_t st = (cudaStream_t)stream;
     const bool sorted = P.W <= SMAXW;
@@ -1537,6 +1585,7 @@ int gdi_launch_grid_anneal(const GdiDevProblem &P, const GdiDevRun &R, const Gdi
         A.nrep = nrep;
         A.spc = spc;
         A.wpc = wpc;
+        A.wbnd = sorted ? wbnd : nullptr;
         void *args[] = {&A};
         e = cudaLaunchCooperativeKernel(kern, dim3(sms), dim3(GB), args, smem, st);
         if (e != cudaSuccess) return (int)e;

@@ -76,9 +76,18 @@ int gdi_launch_init(const GdiDevProblem &P, int8_t *spins, const int8_t *init_or
 int gdi_launch_cta_anneal(const GdiDevProblem &P, const GdiDevRun &R, int block, int grid_limit,
                           void *stream, int *grid_used, size_t *smem_used);
 int gdi_cta_smem_bytes(const GdiDevProblem &P, const GdiDevRun &R, int block, size_t *bytes, int *hist);
-int gdi_grid_plan(const GdiDevProblem &P, int max_row, int sms, int *spc, int *wpc, size_t *smem);
+// Grid plan for `sms` blocks: spans of ranks (spc) and windows (wpc) per block and per class, and
+// the dynamic shared memory; -1 if the instance does not fit smem_limit.
+int gdi_grid_plan(const GdiDevProblem &P, int max_row, int sms, size_t smem_limit, int *spc, int *wpc,
+                  size_t *smem);
+// Host: first window of every block, per class, for the sorted-window grid path.  cost[k] is the
+// cost of window k of the class (windows of one class consecutive, class c starting at
+// cost_off[c]); every block gets at most wpc windows.  bnd has num_classes * (blocks + 1) entries.
+void gdi_grid_window_bounds(const int64_t *cost, const int64_t *cost_off, int num_classes, int blocks,
+                            int wpc, int32_t *bnd);
 int gdi_launch_grid_anneal(const GdiDevProblem &P, const GdiDevRun &R, const GdiGridScratch &X,
-                           int8_t *spins, int sms, int spc, int wpc, size_t smem, void *stream);
+                           int8_t *spins, int sms, int spc, int wpc, size_t smem, const int32_t *wbnd,
+                           void *stream);
 int gdi_launch_grid_finish(const GdiDevProblem &P, const GdiDevRun &R, const GdiGridScratch &X,
                            int8_t *spins, int do_repair, void *stream);
 int gdi_launch_gather_spins(const GdiDevProblem &P, const int8_t *spins_rank, int8_t *out_orig,

@@ -119,7 +119,7 @@ extern "C" int gdi_anneal_static(int32_t n, const int64_t *row_ptr, const uint32
     P.max_class = max_class;
     int spc = 0, wpc = 0;
     size_t smem = 0;
-    if (gdi_grid_plan(P, max_row, nblk, &spc, &wpc, &smem) != 0 || smem > (size_t)optin)
+    if (gdi_grid_plan(P, max_row, nblk, (size_t)optin, &spc, &wpc, &smem) != 0)
         return gdi_set_error(GDI_ERR_TOO_LARGE, "gdi_anneal_static: the plan needs " + std::to_string(smem) +
                                                     " bytes of shared memory per block; use a smaller W");
 
@@ -167,7 +167,7 @@ extern "C" int gdi_anneal_static(int32_t n, const int64_t *row_ptr, const uint32
     e = cudaMemsetAsync(X.err, 0, sizeof(int32_t), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(X.status, 0, 16 * sizeof(int32_t), st);
     if (e != cudaSuccess) return gdi_set_error(GDI_ERR_CUDA, std::string("gdi_anneal_static: ") + cudaGetErrorString(e));
-    const int ke = gdi_launch_grid_anneal(P, R, X, spins, nblk, spc, wpc, smem, st);
+    const int ke = gdi_launch_grid_anneal(P, R, X, spins, nblk, spc, wpc, smem, nullptr, st);
     if (ke) return gdi_set_error(GDI_ERR_CUDA, std::string("gdi_anneal_static launch: ") +
                                                    cudaGetErrorString((cudaError_t)ke));
     return GDI_OK;
