@@ -147,25 +147,23 @@ __device__ __forceinline__ void field8_thread(const GdiDevProblem &P, int64_t ba
         cN6 += (int32_t)((aN >> 48) & 0xFF); cN7 += (int32_t)((aN >> 56) & 0xFF);                 \
         aP = aN = 0;                                                                              \
     } while (0)
-    int64_t e = e0;
-    for (; e + 4 <= e1; e += 4) {
-        const uint32_t c0 = __ldg(P.col + e), c1 = __ldg(P.col + e + 1);
-        const uint32_t c2 = __ldg(P.col + e + 2), c3 = __ldg(P.col + e + 3);
-        const uint64_t s0 = spread8(__ldcg(packed + base + (c0 & 0x7FFFFFFFu)));
-        const uint64_t s1 = spread8(__ldcg(packed + base + (c1 & 0x7FFFFFFFu)));
-        const uint64_t s2 = spread8(__ldcg(packed + base + (c2 & 0x7FFFFFFFu)));
-        const uint64_t s3 = spread8(__ldcg(packed + base + (c3 & 0x7FFFFFFFu)));
-        if (c0 >> 31) { aN += s0; ++nN; } else aP += s0;
-        if (c1 >> 31) { aN += s1; ++nN; } else aP += s1;
-        if (c2 >> 31) { aN += s2; ++nN; } else aP += s2;
-        if (c3 >> 31) { aN += s3; ++nN; } else aP += s3;
-        cnt += 4;
-        if (cnt >= 252) { GDI_FLUSH(); cnt = 0; }
-    }
-    for (; e < e1; ++e) {
-        const uint32_t c = __ldg(P.col + e);
-        const uint64_t sv = spread8(__ldcg(packed + base + (c & 0x7FFFFFFFu)));
-        if (c >> 31) { aN += sv; ++nN; } else aP += sv;
+    // predicated batches of 8 entries: every load of a batch is in flight at once (rows of up to 8
+    // entries cost one round trip for the columns and one for the spins)
+    for (int64_t e = e0; e < e1; e += 8) {
+        const int nb = (int)min((int64_t)8, e1 - e);
+        uint32_t c[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) c[k] = k < nb ? __ldg(P.col + e + k) : 0u;
+        uint8_t b[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) b[k] = k < nb ? __ldcg(packed + base + (c[k] & 0x7FFFFFFFu)) : (uint8_t)0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const uint64_t sv = spread8(b[k]);
+            if (c[k] >> 31) { aN += sv; ++nN; } else aP += sv;
+        }
+        cnt += 8;
+        if (cnt >= 248) { GDI_FLUSH(); cnt = 0; }
     }
     GDI_FLUSH();
 #undef GDI_FLUSH
