@@ -125,12 +125,11 @@ __device__ bool grid_sync(const GdiGridScratch &X)
     return ok != 0;
 }
 
-// local fields of one rank for all 8 replicas (thread-serial over the row, four neighbours in
-// flight at a time), written to hout[0..7] (all replicas) or hout[0] (replica `one` only)
-__device__ __forceinline__ void field8_thread(const GdiDevProblem &P, int64_t base, int32_t r,
+// local fields of one rank (row entries [e0, e1)) for all 8 replicas, thread-serial over the row,
+// written to hout[0..7] (all replicas) or hout[0] (replica `one` only)
+__device__ __forceinline__ void field8_thread(const GdiDevProblem &P, int64_t base, int64_t e0, int64_t e1,
                                               const uint8_t *packed, int16_t *hout, int one)
 {
-    const int64_t e0 = P.row_ptr[base + r], e1 = P.row_ptr[base + r + 1];
     uint64_t aP = 0, aN = 0;
     int32_t nN = 0, cnt = 0;
     int32_t cP0 = 0, cP1 = 0, cP2 = 0, cP3 = 0, cP4 = 0, cP5 = 0, cP6 = 0, cP7 = 0;
@@ -395,7 +394,8 @@ struct GSmem {
     int32_t *longq;    // [spc]
     int16_t *wtab;     // [wpc][8][TW]
     int32_t *win;      // [wpc][8]
-    int32_t *hist;     // [NWARP][2][HB]
+    int32_t *hist;     // [NWARP][2][HB] (tabulated path) or [NWARP][HA] (sorted path)
+    int32_t *nchunk;   // [spc] chunk counts of the long rows
     int16_t *ctab;     // [P][TW]
     uint32_t *row;     // [max_row]
     int64_t *misc;     // scratch
@@ -433,11 +433,11 @@ __device__ void range_thresholds(const GridArgs &A, const GSmem &S, int32_t a0, 
     for (int32_t i = threadIdx.x; i < ns; i += GB) {
         const int32_t rk = a0 + i;
         s0_out[i] = __ldcg(packed + base + rk);
-        const int64_t deg = P.row_ptr[base + rk + 1] - P.row_ptr[base + rk];
-        if (all_reps && deg > LONG_ROW) {
+        const int64_t e0 = P.row_ptr[base + rk], e1 = P.row_ptr[base + rk + 1];
+        if (all_reps && e1 - e0 > LONG_ROW) {
             S.longq[atomicAdd(&nlong, 1)] = i;
         } else {
-            field8_thread(P, base, rk, packed, all_reps ? hbuf + (size_t)i * 8 : hbuf + i, all_reps ? -1 : one);
+            field8_thread(P, base, e0, e1, packed, all_reps ? hbuf + (size_t)i * 8 : hbuf + i, all_reps ? -1 : one);
         }
     }
     __syncthreads();
@@ -448,7 +448,7 @@ __device__ void range_thresholds(const GridArgs &A, const GSmem &S, int32_t a0, 
         // field slots; the chunk count of long row t is kept in the histogram area.
         const int nl = nlong;
         int32_t *acc = gam_out;
-        int32_t *nchunk = S.hist;                // [nl] (spc <= NWARP * 2 * HB, checked by the plan)
+        int32_t *nchunk = S.nchunk;              // [nl]
         for (int t = threadIdx.x; t < nl; t += GB) {
             const int32_t i = S.longq[t];
             const int64_t deg = P.row_ptr[base + a0 + i + 1] - P.row_ptr[base + a0 + i];
@@ -659,6 +659,7 @@ __global__ void __launch_bounds__(GB, 1) gdi_grid_anneal_kernel(GridArgs A)
     S.wtab = reinterpret_cast<int16_t *>(smem_raw + L.off_wtab);
     S.win = reinterpret_cast<int32_t *>(smem_raw + L.off_win);
     S.hist = reinterpret_cast<int32_t *>(smem_raw + L.off_hist);
+    S.nchunk = S.hist;   // spc <= NWARP * 2 * HB, checked by the plan
     S.ctab = reinterpret_cast<int16_t *>(smem_raw + L.off_ctab);
     S.row = reinterpret_cast<uint32_t *>(smem_raw + L.off_row);
     S.misc = reinterpret_cast<int64_t *>(smem_raw + L.off_misc);
@@ -871,9 +872,9 @@ __host__ __device__ inline SortedLayout sorted_layout(int spc, int wpc, int max_
     L.off_fm = o; o = align16(o + (size_t)((spc + 3) / 4) * sizeof(uint32_t));
     L.fw = spc / 32 + 2;
     L.off_fbits = o; o = align16(o + (size_t)8 * L.fw * sizeof(uint32_t));
-    L.off_longq = o; o = align16(o + (size_t)spc * sizeof(int32_t));
+    L.off_longq = o; o = align16(o + (size_t)2 * spc * sizeof(int32_t));   // long rows, chunk counts
     L.off_smap = o; o = align16(o + (size_t)wpc * 8 * 2 * sizeof(StageMap));
-    L.off_hist = o; o = align16(o + (size_t)NWARP * 2 * HB * sizeof(int32_t));
+    L.off_hist = o; o = align16(o + (size_t)NWARP * HA * sizeof(int32_t));    // exact-replay bins
     L.off_walk = o; o = align16(o + (size_t)8 * walk_slots(P) * NT);
     L.off_row = o; o = align16(o + (size_t)(max_row + 4) * sizeof(uint32_t));
     L.off_misc = o; o = align16(o + 64 * sizeof(int64_t));
@@ -1089,6 +1090,7 @@ __global__ void __launch_bounds__(GB, 1) gdi_grid_sorted_kernel(GridArgs A)
     GSmem S = {};
     S.longq = reinterpret_cast<int32_t *>(smem_raw + L.off_longq);
     S.hist = hist;
+    S.nchunk = S.longq + spc;
     S.row = reinterpret_cast<uint32_t *>(smem_raw + L.off_row);
     S.misc = reinterpret_cast<int64_t *>(smem_raw + L.off_misc);
     int32_t *Gc = reinterpret_cast<int32_t *>(S.misc);   // [8] class-start G of each replica
@@ -1246,7 +1248,7 @@ __global__ void __launch_bounds__(GB, 1) gdi_grid_sorted_kernel(GridArgs A)
                     int32_t x = gin - c0;
                     const int32_t *gr = gam + (size_t)r * spc;
                     const int16_t *rr = hb + (size_t)r * spc;
-                    int32_t *bins = hist + (size_t)warp * 2 * HB;
+                    int32_t *bins = hist + (size_t)warp * HA;
                     for (int kk = 0; kk < nwin; ++kk) {
                         const int ws = kk * W, we = min(ws + W, ns);
                         if (x >= -FAST_X && x <= FAST_X) {
@@ -1502,16 +1504,16 @@ int gdi_grid_plan(const GdiDevProblem &P, int max_row, int sms, size_t smem_limi
     const int w = (wp + sms - 1) / sms;
     *wpc = w < 1 ? 1 : w;
     *spc = *wpc * P.W;
-    // long rows keep their chunk counts in the histogram area
-    if ((size_t)*spc > (size_t)NWARP * 2 * HB) return -1;
     if (P.W <= SMAXW) {
         // the cost-weighted split stays within the even share of windows per block: more shared
         // memory per block (less L1) costs more than the finer balance gains
         *smem = sorted_layout(*spc, *wpc, max_row, sms).total;
         return *smem <= smem_limit ? 0 : -1;
     }
-    // the exact chain fallback of the tabulated path keeps thresholds, fields, start signs and bins
-    // of one block's windows (one replica) in the histogram area
+    // the tabulated path keeps the long rows' chunk counts in the histogram area, and its exact
+    // chain fallback the thresholds, fields, start signs and bins of one block's windows (one
+    // replica)
+    if ((size_t)*spc > (size_t)NWARP * 2 * HB) return -1;
     if ((size_t)*spc * 7 + 64 + HA * sizeof(int32_t) > (size_t)NWARP * 2 * HB * sizeof(int32_t)) return -1;
     *smem = grid_layout(*spc, *wpc, sms, max_row).total;
     return *smem <= smem_limit ? 0 : -1;
