@@ -572,7 +572,7 @@ __device__ int32_t window_exact(const int32_t *gam, int gs, int gc, const uint8_
 }
 
 // G of every replica: n - 2 #(-1), accumulated into X.Gcls (zeroed by the host)
-__device__ void init_G(const GridArgs &A, int p, int Pb, int32_t n, int64_t base)
+__device__ __noinline__ void init_G(const GridArgs &A, int p, int Pb, int32_t n, int64_t base)
 {
     const GdiGridScratch &X = A.X;
     const int lane = threadIdx.x & 31;
@@ -593,7 +593,7 @@ __device__ void init_G(const GridArgs &A, int p, int Pb, int32_t n, int64_t base
 }
 
 // digest and cut of every replica after sweep sw (grid-wide atomics), and G after the sweep
-__device__ void sweep_trace(const GridArgs &A, int p, int Pb, int32_t n, int64_t base, int sw)
+__device__ __noinline__ void sweep_trace(const GridArgs &A, int p, int Pb, int32_t n, int64_t base, int sw)
 {
     const GdiDevProblem &P = A.P;
     const GdiDevRun &R = A.R;
@@ -1069,6 +1069,18 @@ __device__ __forceinline__ bool poll_flags(const uint32_t *f, int cnt, uint32_t 
     return __all_sync(0xFFFFFFFFu, ok);
 }
 
+// the exact replay of one window by counting (|G - c| beyond the stored values), kept out of line
+__device__ __noinline__ int32_t window_replay_exact(const int32_t *gr, const uint8_t *s0, int r, int ws, int we,
+                                                    int32_t g, bool plus_first, int32_t *bins, uint32_t *fm)
+{
+    const int32_t K1 = warp_group(gr, 1, 0, s0, r, ws, we, g, plus_first, bins, fm);
+    g = plus_first ? g - 2 * K1 : g + 2 * K1;
+    const int32_t K2 = warp_group(gr, 1, 0, s0, r, ws, we, g, !plus_first, bins, fm);
+    return plus_first ? g + 2 * K2 : g - 2 * K2;
+}
+
+// SL = members per lane of a window sort (1, 2, 4 or 8): one instantiation per window size class
+template <int SL>
 __global__ void __launch_bounds__(GB, 1) gdi_grid_sorted_kernel(GridArgs A)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1109,7 +1121,6 @@ __global__ void __launch_bounds__(GB, 1) gdi_grid_sorted_kernel(GridArgs A)
     const int32_t ncls = P.class_off[1] - P.class_off[0] - 1;
     const int W = P.W;
     const int nrep = A.nrep;
-    const int SL = W <= 32 ? 1 : W <= 64 ? 2 : W <= 128 ? 4 : 8;
 
     init_G(A, p, Pb, n, base);
     if (!grid_sync(X)) return;
@@ -1146,10 +1157,7 @@ __global__ void __launch_bounds__(GB, 1) gdi_grid_sorted_kernel(GridArgs A)
                 const int32_t *gr = gam + (size_t)r * spc;
                 int16_t *rr = hb + (size_t)r * spc;
                 StageMap *o = smap + ((size_t)kk * 8 + r) * 2;
-                if (SL == 1) window_maps<1>(gr, s0, rr, ws, wlen, r, Gc[r], o);
-                else if (SL == 2) window_maps<2>(gr, s0, rr, ws, wlen, r, Gc[r], o);
-                else if (SL == 4) window_maps<4>(gr, s0, rr, ws, wlen, r, Gc[r], o);
-                else window_maps<8>(gr, s0, rr, ws, wlen, r, Gc[r], o);
+                window_maps<SL>(gr, s0, rr, ws, wlen, r, Gc[r], o);
             }
             for (int i = threadIdx.x; i < (ns + 3) / 4; i += GB) fm[i] = 0;
             for (int i = threadIdx.x; i < 8 * L.fw; i += GB) fbits[i] = 0;
@@ -1277,12 +1285,7 @@ __global__ void __launch_bounds__(GB, 1) gdi_grid_sorted_kernel(GridArgs A)
                                 x = plus ? x - 2 * cnt : x + 2 * cnt;
                             }
                         } else {
-                            int32_t g = c0 + x;
-                            const int32_t K1 = warp_group(gr, 1, 0, s0, r, ws, we, g, plus_first, bins, fm);
-                            g = plus_first ? g - 2 * K1 : g + 2 * K1;
-                            const int32_t K2 = warp_group(gr, 1, 0, s0, r, ws, we, g, !plus_first, bins, fm);
-                            g = plus_first ? g + 2 * K2 : g - 2 * K2;
-                            x = g - c0;
+                            x = window_replay_exact(gr, s0, r, ws, we, c0 + x, plus_first, bins, fm) - c0;
                         }
                     }
                     const int32_t gout = c0 + x;
@@ -1561,7 +1564,11 @@ int gdi_launch_grid_anneal(const GdiDevProblem &P, const GdiDevRun &R, const Gdi
 {
     cudaStream_t st = (cudaStream_t)stream;
     const bool sorted = P.W <= SMAXW;
-    const void *kern = sorted ? (const void *)gdi_grid_sorted_kernel : (const void *)gdi_grid_anneal_kernel;
+    const void *kern = !sorted ? (const void *)gdi_grid_anneal_kernel
+                     : P.W <= 32 ? (const void *)gdi_grid_sorted_kernel<1>
+                     : P.W <= 64 ? (const void *)gdi_grid_sorted_kernel<2>
+                     : P.W <= 128 ? (const void *)gdi_grid_sorted_kernel<4>
+                                  : (const void *)gdi_grid_sorted_kernel<8>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return (int)e;
     int per_sm = 0;
