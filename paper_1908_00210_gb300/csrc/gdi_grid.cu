@@ -4,21 +4,28 @@
 // colour classes in order, windows of W ranks, inside a window the +1 group by threshold ascending
 // then the -1 group by threshold descending, each seeing the exact running G).  What changes is
 // how the chain of windows is evaluated when a class holds thousands of windows spread over every
-// SM:
+// SM.  Common to both variants below: up to 8 replicas share one byte per vertex (bit r set = spin
+// of replica r is -1), so one gather of a neighbour byte feeds all of them (SWAR byte-lane
+// counters); every block owns a contiguous run of windows of each class; the map "G at window
+// start -> G at window end" is monotone and is tabulated around c, the G at class start.
 //
-//   * up to 8 replicas share one byte per vertex (bit r set = spin of replica r is -1), so one
-//     gather of a neighbour byte feeds all of them (SWAR byte-lane counters);
-//   * the map "G at window start -> G at window end" of a window is monotone; every window
-//     tabulates it for G in [c - RT, c + RT] (c = G at class start) from two small histograms of
-//     its thresholds, and each block composes the maps of its consecutive windows;
+// Sorted-window variant (W <= 256, gdi_grid_sorted_kernel): a warp sorts each (window, replica)
+// group once, after which every member decides its own flip by one comparison; block tables are
+// published with release flags and each block finds its entering G by looking them up, so only
+// one grid barrier per class remains (described before the kernel).
+//
+// Tabulated variant (W > 256, gdi_grid_anneal_kernel):
+//   * every window tabulates its map for G in [c - RT, c + RT] from two small histograms of its
+//     thresholds, and each block composes the maps of its consecutive windows;
 //   * after a grid barrier one block per replica walks the P block maps (a few hundred
 //     shared-memory lookups) and publishes every block's exact input G; an entry that left the
 //     tabulated range is recomputed exactly from the spins (fallback);
 //   * after a second barrier every block replays its windows with the exact input, flips, and a
 //     third barrier makes the class's spins visible to the next class.
 //
-// Grid barriers are sense/generation barriers on global counters with a bounded spin: a block that
-// waits too long sets the error word and the kernel returns (GDI_ERR_TIMEOUT on the host).
+// Grid barriers are sense/generation barriers on global counters with a bounded spin, and every
+// flag wait is bounded too: a block that waits too long sets the error word and the kernel returns
+// (GDI_ERR_TIMEOUT on the host).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -29,7 +36,7 @@ using namespace gdi;
 
 namespace {
 
-constexpr int GB = 512;                 // threads per block
+constexpr int GB = 768;                 // threads per block
 constexpr int NWARP = GB / 32;
 constexpr int RT = 64;                  // tables cover G in [c - RT, c + RT]
 constexpr int TW = 2 * RT + 1;
