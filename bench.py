@@ -33,7 +33,9 @@ WORKLOADS = {
     # 500 sweeps, window W = 256: the grid-scale path (every SM on one graph)
     "ba1m_r8": dict(kind="ba", n=1_000_000, m=5, gseed=4004, A=1, B=4, W=256, replicas=8,
                     sweeps=500, t0=12.0, t1=0.2, seed=1,
-                    roofline=dict(bound="hbm", bytes_per_update=56)),
+                    # traffic: dram__bytes_read.sum + dram__bytes_write.sum of one 500-sweep launch
+                    # of gdi_grid_sorted_kernel<8> (ncu, profiles/gdi_grid_sorted_kernel_ba1m_r8.md)
+                    roofline=dict(bound="hbm", bytes_per_update=56, traffic=49873152 + 397312)),
     # 2-D torus 100 x 100, +-1 weights, checkerboard colouring, 64 replicas, 5000 sweeps
     "torus100_r64": dict(kind="torus", L=100, gseed=2002, A=1, B=4, W=1024, replicas=64,
                          sweeps=5000, t0=12.0, t1=0.2, seed=1,
@@ -244,6 +246,7 @@ def run_ours(args, wl, rank, world, local):
     clocks.start()
     wall0 = time.perf_counter()
     ms = []
+    kms, klaunch = 0.0, 0                               # the sweep kernel alone (library events)
     launches = 0
     with torch.cuda.stream(stream):
         for _ in range(args.steps):
@@ -256,6 +259,9 @@ def run_ours(args, wl, rank, world, local):
             launches += launches_per_anneal(launch_path, wl["replicas"])
             e1.synchronize()
             ms.append(e0.elapsed_time(e1))
+            k_ms, k_n = ann.kernel_ms()
+            kms += k_ms
+            klaunch += k_n
     torch.cuda.synchronize()
     barrier(world)
     torch.cuda.synchronize()
@@ -295,20 +301,24 @@ def run_ours(args, wl, rank, world, local):
         return
     pk = peaks()
     rf = wl["roofline"]
-    rate = updates / (ms_per_step / 1e3)
+    # roofline of the dominant kernel: algorithmic bytes (ops) of one launch / its mean duration,
+    # from CUDA events recorded by the library around each sweep-kernel launch on this stream
+    kernel_ms = kms / max(1, klaunch)
+    rate = updates * args.steps / max(1, klaunch) / (kernel_ms / 1e3)
     if rf["bound"] == "hbm":
         peak = float(pk.get("hbm_gbs", 6800.0))
         achieved = rf["bytes_per_update"] * rate / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None,
-                "bytes_per_update": rf["bytes_per_update"],
+                "frac": achieved / peak, "traffic": rf.get("traffic"),
+                "bytes_per_update": rf["bytes_per_update"], "kernel_ms_per_launch": kernel_ms,
                 "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
     else:
         sm_max = float(pk.get("sm_max_mhz", 2070.0))
         peak = dev_props.multi_processor_count * 128 * sm_max * 1e6 / 1e12
         achieved = rf["ops_per_update"] * rate / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
-                "frac": achieved / peak, "traffic": None, "ops_per_update": rf["ops_per_update"],
+                "frac": achieved / peak, "traffic": rf.get("traffic"), "ops_per_update": rf["ops_per_update"],
+                "kernel_ms_per_launch": kernel_ms,
                 "peak_note": "SMs x 128 int32 lanes x max SM clock (derived)"}
     try:
         if args.quick:
@@ -343,8 +353,11 @@ def run_ours(args, wl, rank, world, local):
 # kernels of ours per gdi_anneal: CTA path = init + anneal; grid path = init + (pack + anneal +
 # unpack) per 8-replica group + raw cut + repair (hist, select, ties, mark, apply) + final cut
 def launches_per_anneal(path: int, replicas: int) -> int:
+    """Kernels of one gdi_anneal: grid path = initial spins, then per group of 8 replicas pack,
+    sweep kernel, raw cut, unpack, five repair kernels, pack and final cut; CTA path = initial
+    spins and the persistent sweep kernel (cut and repair inside it)."""
     if path == 2:
-        return 1 + 3 * ((replicas + 7) // 8) + 1 + 5 + 1
+        return 1 + 11 * ((replicas + 7) // 8)
     return 2
 
 

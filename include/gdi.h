@@ -159,6 +159,14 @@ int gdi_autotune(gdi_ctx *ctx, const gdi_schedule *schedule, int32_t probe_sweep
 int gdi_last_launch(gdi_ctx *ctx, int32_t *path, int32_t *grid, int64_t *smem_bytes,
                     int32_t *fallbacks);
 
+/* Device time of the anneal kernel launches of the last gdi_anneal (the sweep kernels alone,
+ * without the initialisation, packing, cut and repair kernels around them), measured with CUDA
+ * events recorded on the anneal's stream around every launch: *ms = their sum, *launches = how
+ * many (one per group of 8 replicas on the grid-scale path, one on the CTA path; may be NULL).
+ * GDI_ERR_NOT_ANNEALED if there was no anneal, or if it was captured into a CUDA graph (no
+ * events are recorded while a stream is being captured).  Synchronises. */
+int gdi_kernel_time(gdi_ctx *ctx, float *ms, int32_t *launches);
+
 /* Context facts: number of colour classes per instance (host [num_instances], may be NULL),
  * the largest degree, and the E_cap of the last schedule (0 before any anneal). */
 int gdi_info(gdi_ctx *ctx, int32_t *num_classes, int32_t *max_degree, int32_t *ecap);

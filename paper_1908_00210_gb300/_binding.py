@@ -27,7 +27,7 @@ ERRORS = {
 # every entry point that include/gdi.h declares
 EXPORTS = ["gdi_create", "gdi_anneal", "gdi_get_spins", "gdi_get_results", "gdi_cut", "gdi_balance",
            "gdi_get_trace", "gdi_configure", "gdi_last_launch", "gdi_info", "gdi_destroy",
-           "gdi_strerror", "gdi_last_error", "gdi_anneal_static", "gdi_autotune"]
+           "gdi_strerror", "gdi_last_error", "gdi_anneal_static", "gdi_autotune", "gdi_kernel_time"]
 GDI_PATH_AUTO, GDI_PATH_CTA, GDI_PATH_GRID = 0, 1, 2
 
 
@@ -83,6 +83,7 @@ def load():
     L.gdi_anneal_static.argtypes = [i32, vp, vp, i32, vp, i32, i32, i32, i32, i32, i32, vp, vp, vp,
                                     i32, i32, i32, i32, C.c_uint64, i32, vp, vp, vp]
     L.gdi_last_launch.argtypes = [vp, vp, vp, vp, vp]
+    L.gdi_kernel_time.argtypes = [vp, vp, vp]
     L.gdi_destroy.argtypes = [vp]
     L.gdi_destroy.restype = None
     L.gdi_strerror.argtypes = [C.c_int]
@@ -247,6 +248,13 @@ class Annealer:
         fb = np.zeros(1, np.int32)
         _check(load().gdi_last_launch(self._h, pa.ctypes.data, gr.ctypes.data, sm.ctypes.data, fb.ctypes.data))
         return dict(path=int(pa[0]), grid=int(gr[0]), smem=int(sm[0]), fallbacks=int(fb[0]))
+
+    def kernel_ms(self):
+        """Device time (ms) of the last anneal's sweep-kernel launches and their number."""
+        ms = np.zeros(1, np.float32)
+        n = np.zeros(1, np.int32)
+        _check(load().gdi_kernel_time(self._h, ms.ctypes.data, n.ctypes.data))
+        return float(ms[0]), int(n[0])
 
     def info(self):
         nc = np.zeros(self.num_instances, np.int32)

@@ -84,6 +84,9 @@ struct gdi_ctx {
     std::vector<int64_t> wcost, wcost_off;
     DevBuf<int32_t> g_wbnd;
     int wbnd_blocks = 0, wbnd_wpc = 0;
+    // events around the anneal kernel launches of the last gdi_anneal (none while capturing)
+    std::vector<cudaEvent_t> kev;
+    int kev_pairs = 0;
     std::vector<int32_t> num_classes;       // per instance
     DevBuf<int64_t> node_off, row_ptr;
     DevBuf<int32_t> class_off, class_ptr, rank_of;
@@ -142,6 +145,9 @@ struct gdi_ctx {
         err.release(); raw_cut.release(); final_cut.release(); tr_cut.release(); tr_digest.release();
         g_packed.release(); g_rflags.release(); g_tables.release(); g_gin.release(); g_Gcls.release();
         g_wbnd.release();
+        for (cudaEvent_t ev : kev) cudaEventDestroy(ev);
+        kev.clear();
+        kev_pairs = 0;
         g_err.release(); g_status.release(); g_rhist.release(); g_rties.release(); g_rparams.release();
         g_bar.release();
         item_order.release(); item_counter.release();
@@ -633,14 +639,35 @@ int gdi_anneal(gdi_ctx *c, const gdi_schedule *S, const gdi_run *run)
     bool grid = false;
     if (c->path == GDI_PATH_GRID) grid = true;
     else if (c->path == GDI_PATH_AUTO) grid = (c->Q == 1 && (c->max_n > 32768 || need > (size_t)max_optin));
+    // kernel timing events (not while the stream is being captured into a graph)
+    GdiKernelTimer timer{nullptr, 0, 0};
+    c->kev_pairs = 0;
+    {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone) {
+            const size_t want = 2 * (size_t)std::max(1, (c->R + 7) / 8);
+            while (c->kev.size() < want) {
+                cudaEvent_t ev;
+                if (cudaEventCreate(&ev) != cudaSuccess) break;
+                c->kev.push_back(ev);
+            }
+            if (c->kev.size() >= want) timer = GdiKernelTimer{c->kev.data(), (int)(c->kev.size() / 2), 0};
+        }
+        cudaGetLastError();
+    }
     if (!grid) {
         cudaMemsetAsync(c->item_counter.p, 0, sizeof(int32_t), st);
         if (need > (size_t)max_optin)
             return fail(GDI_ERR_TOO_LARGE, "instance needs " + std::to_string(need) +
                                                " bytes of shared memory per block (limit " +
                                                std::to_string(max_optin) + "); use one instance with W > 0");
+        if (timer.ev) cudaEventRecord(timer.ev[0], st);
         int ke = gdi_launch_cta_anneal(P, R, c->block, c->grid_limit, st, &c->last_grid, &c->last_smem);
         if (ke) return cuda_fail((cudaError_t)ke, "anneal kernel launch");
+        if (timer.ev) {
+            cudaEventRecord(timer.ev[1], st);
+            timer.n = 1;
+        }
         c->used_grid = false;
     } else {
         if (c->Q != 1 || c->W < 1)
@@ -683,7 +710,7 @@ int gdi_anneal(gdi_ctx *c, const gdi_schedule *S, const gdi_run *run)
             }
             wbnd = c->g_wbnd.p;
         }
-        int ke = gdi_launch_grid_anneal(P, R, X, c->spins.p, nblk, spc, wpc, smem, wbnd, st);
+        int ke = gdi_launch_grid_anneal(P, R, X, c->spins.p, nblk, spc, wpc, smem, wbnd, &timer, st);
         if (ke) return cuda_fail((cudaError_t)ke, "grid anneal launch");
         ke = gdi_launch_grid_finish(P, R, X, c->spins.p, (run->flags & GDI_FLAG_NO_REPAIR) ? 0 : 1, st);
         if (ke) return cuda_fail((cudaError_t)ke, "grid finish kernels");
@@ -691,6 +718,7 @@ int gdi_anneal(gdi_ctx *c, const gdi_schedule *S, const gdi_run *run)
         c->last_grid = nblk;
         c->last_smem = smem;
     }
+    c->kev_pairs = timer.n;
     c->stream = st;
     c->annealed = true;
     c->last_sweeps = S->sweeps;
@@ -884,6 +912,25 @@ int gdi_last_launch(gdi_ctx *c, int32_t *path, int32_t *grid, int64_t *smem_byte
             for (int i = 0; i < 8; ++i) *fallbacks += st[i];
         }
     }
+    return GDI_OK;
+}
+
+int gdi_kernel_time(gdi_ctx *c, float *ms, int32_t *launches)
+{
+    if (!c || !ms) return fail(GDI_ERR_INVALID_ARG, "null argument");
+    if (!c->annealed) return fail(GDI_ERR_NOT_ANNEALED, "no anneal yet");
+    int rc = sync_ctx(c);
+    if (rc) return rc;
+    if (c->kev_pairs < 1) return fail(GDI_ERR_NOT_ANNEALED, "the last anneal was not timed (captured into a graph)");
+    float total = 0.f;
+    for (int i = 0; i < c->kev_pairs; ++i) {
+        float t = 0.f;
+        cudaError_t e = cudaEventElapsedTime(&t, c->kev[(size_t)2 * i], c->kev[(size_t)2 * i + 1]);
+        if (e != cudaSuccess) return cuda_fail(e, "kernel events");
+        total += t;
+    }
+    *ms = total;
+    if (launches) *launches = c->kev_pairs;
     return GDI_OK;
 }
 

@@ -1342,8 +1342,45 @@ __global__ void unpack_kernel(int8_t *spins, int64_t N, int rep_base, int nrep, 
     }
 }
 
+// cut of every replica of a group from the packed spins, in one pass over the CSR: for an entry
+// (i, j > i), d = b_i ^ b_j has bit r set where replica r cuts the edge; SWAR byte lanes count the
+// cut weights (flushed before they can overflow)
+__global__ void packed_cut_kernel(GdiDevProblem P, const uint8_t *packed, int nrep, int64_t *cut)
+{
+    const int64_t base = P.node_off[0];
+    const int64_t n = P.node_off[1] - base;
+    int64_t acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint8_t b = packed[base + i];
+        uint64_t aP = 0, aN = 0;
+        int cnt = 0;
+        const int64_t e1 = P.row_ptr[base + i + 1];
+        for (int64_t e = P.row_ptr[base + i]; e < e1; ++e) {
+            const uint32_t c = __ldg(P.col + e);
+            const uint32_t j = c & 0x7FFFFFFFu;
+            if ((int64_t)j <= i) continue;
+            const uint64_t sv = spread8((uint32_t)(b ^ packed[base + j]));
+            if (c >> 31) aN += sv; else aP += sv;
+            if (++cnt == 255) {
+#pragma unroll
+                for (int k = 0; k < 8; ++k)
+                    acc[k] += (int64_t)((aP >> (8 * k)) & 0xFF) - (int64_t)((aN >> (8 * k)) & 0xFF);
+                aP = aN = 0;
+                cnt = 0;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) acc[k] += (int64_t)((aP >> (8 * k)) & 0xFF) - (int64_t)((aN >> (8 * k)) & 0xFF);
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const int64_t v = warp_sum(acc[k]);
+        if (k < nrep && (threadIdx.x & 31) == 0 && v) atomicAdd((unsigned long long *)(cut + k), (unsigned long long)v);
+    }
+}
+
 // ---------------------------------------------------------------------------------------------
-// cut and exact-balance repair of a single large instance, replica by replica (int8 spins)
+// exact-balance repair of a single large instance, replica by replica (int8 spins)
 __device__ __forceinline__ int32_t field_i8(const GdiDevProblem &P, const int8_t *s, int64_t r)
 {
     int32_t h = 0;
@@ -1353,24 +1390,6 @@ __device__ __forceinline__ int32_t field_i8(const GdiDevProblem &P, const int8_t
         h += (c >> 31) ? -v : v;
     }
     return h;
-}
-
-__global__ void cut_kernel(GdiDevProblem P, const int8_t *spins, int nrep, int64_t *cut)
-{
-    const int64_t N = P.N;
-    for (int r = 0; r < nrep; ++r) {
-        const int8_t *s = spins + (int64_t)r * N;
-        int64_t c = 0;
-        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
-            for (int64_t e = P.row_ptr[i]; e < P.row_ptr[i + 1]; ++e) {
-                const uint32_t cc = __ldg(P.col + e);
-                const int64_t j = cc & 0x7FFFFFFFu;
-                if (j > i && s[j] != s[i]) c += (cc >> 31) ? -1 : 1;
-            }
-        }
-        c = warp_sum(c);
-        if ((threadIdx.x & 31) == 0 && c) atomicAdd((unsigned long long *)(cut + r), (unsigned long long)c);
-    }
 }
 
 // per replica: k = (|G| - n mod 2) / 2 majority spins with the smallest (s h, rank) keys flip.
@@ -1567,7 +1586,7 @@ void gdi_grid_window_bounds(const int64_t *cost, const int64_t *cost_off, int nu
 
 int gdi_launch_grid_anneal(const GdiDevProblem &P, const GdiDevRun &R, const GdiGridScratch &X,
                            int8_t *spins, int sms, int spc, int wpc, size_t smem, const int32_t *wbnd,
-                           void *stream)
+                           GdiKernelTimer *timer, void *stream)
 {
     cudaStream_t st = (cudaStream_t)stream;
     const bool sorted = P.W <= SMAXW;
@@ -1601,8 +1620,15 @@ int gdi_launch_grid_anneal(const GdiDevProblem &P, const GdiDevRun &R, const Gdi
         A.wpc = wpc;
         A.wbnd = sorted ? wbnd : nullptr;
         void *args[] = {&A};
+        const bool timed = timer && timer->ev && timer->n < timer->cap;
+        if (timed) cudaEventRecord(timer->ev[2 * timer->n], st);
         e = cudaLaunchCooperativeKernel(kern, dim3(sms), dim3(GB), args, smem, st);
         if (e != cudaSuccess) return (int)e;
+        if (timed) cudaEventRecord(timer->ev[2 * timer->n++ + 1], st);
+        if (R.raw_cut) {
+            cudaMemsetAsync(R.raw_cut + g0, 0, nrep * sizeof(int64_t), st);
+            packed_cut_kernel<<<152 * 4, 256, 0, st>>>(P, X.packed, nrep, R.raw_cut + g0);
+        }
         unpack_kernel<<<pg, 256, 0, st>>>(spins, P.N, g0, nrep, X.packed);
         e = cudaMemcpyAsync(R.raw_G + g0, X.Gcls, nrep * sizeof(int32_t), cudaMemcpyDeviceToDevice, st);
         if (e != cudaSuccess) return (int)e;
@@ -1614,31 +1640,35 @@ int gdi_launch_grid_anneal(const GdiDevProblem &P, const GdiDevRun &R, const Gdi
 int gdi_launch_grid_finish(const GdiDevProblem &P, const GdiDevRun &R, const GdiGridScratch &X,
                            int8_t *spins, int do_repair, void *stream)
 {
+    // the raw cut was taken from the packed spins right after each group's anneal launch
     cudaStream_t st = (cudaStream_t)stream;
     const int nb = 152 * 4;
     const int64_t N = P.N;
     const int D = P.max_degree;
-    cudaError_t e = cudaMemsetAsync(R.raw_cut, 0, P.replicas * sizeof(int64_t), st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(R.final_cut, 0, P.replicas * sizeof(int64_t), st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(R.final_G, R.raw_G, P.replicas * sizeof(int32_t), cudaMemcpyDeviceToDevice, st);
+    cudaError_t e = cudaMemcpyAsync(R.final_G, R.raw_G, P.replicas * sizeof(int32_t), cudaMemcpyDeviceToDevice, st);
     if (e != cudaSuccess) return (int)e;
-    cut_kernel<<<nb, 256, 0, st>>>(P, spins, P.replicas, R.raw_cut);
-    if (do_repair) {
-        for (int g0 = 0; g0 < P.replicas; g0 += 8) {
-            const int nrep = P.replicas - g0 < 8 ? P.replicas - g0 : 8;
-            int8_t *sp = spins + (int64_t)g0 * N;
-            GdiDevProblem Q = P;
-            cudaMemsetAsync(X.rhist, 0, (size_t)nrep * (2 * D + 1) * sizeof(int32_t), st);
-            cudaMemsetAsync(X.rflags, 0, (size_t)N, st);
-            repair_hist_kernel<<<nb, 256, 0, st>>>(Q, sp, nrep, R.final_G + g0, X.rhist, D);
-            repair_select_kernel<<<nrep, 32, 0, st>>>(R.final_G + g0, N, X.rhist, D, X.rparams);
-            const int64_t chunk = (N + nb - 1) / nb;
-            repair_ties_kernel<<<nb, 256, 0, st>>>(Q, sp, nrep, X.rparams, X.rties, chunk);
-            repair_mark_kernel<<<nb, 256, 0, st>>>(Q, sp, nrep, X.rparams, X.rties, chunk, X.rflags);
-            repair_apply_kernel<<<nb, 256, 0, st>>>(sp, N, nrep, X.rflags, X.rparams, R.final_G + g0);
-        }
+    if (!do_repair) {
+        e = cudaMemcpyAsync(R.final_cut, R.raw_cut, P.replicas * sizeof(int64_t), cudaMemcpyDeviceToDevice, st);
+        return e != cudaSuccess ? (int)e : (int)cudaGetLastError();
     }
-    cut_kernel<<<nb, 256, 0, st>>>(P, spins, P.replicas, R.final_cut);
+    const int pg = (int)((N + 255) / 256) < 4096 ? (int)((N + 255) / 256) : 4096;
+    for (int g0 = 0; g0 < P.replicas; g0 += 8) {
+        const int nrep = P.replicas - g0 < 8 ? P.replicas - g0 : 8;
+        int8_t *sp = spins + (int64_t)g0 * N;
+        GdiDevProblem Q = P;
+        cudaMemsetAsync(X.rhist, 0, (size_t)nrep * (2 * D + 1) * sizeof(int32_t), st);
+        cudaMemsetAsync(X.rflags, 0, (size_t)N, st);
+        repair_hist_kernel<<<nb, 256, 0, st>>>(Q, sp, nrep, R.final_G + g0, X.rhist, D);
+        repair_select_kernel<<<nrep, 32, 0, st>>>(R.final_G + g0, N, X.rhist, D, X.rparams);
+        const int64_t chunk = (N + nb - 1) / nb;
+        repair_ties_kernel<<<nb, 256, 0, st>>>(Q, sp, nrep, X.rparams, X.rties, chunk);
+        repair_mark_kernel<<<nb, 256, 0, st>>>(Q, sp, nrep, X.rparams, X.rties, chunk, X.rflags);
+        repair_apply_kernel<<<nb, 256, 0, st>>>(sp, N, nrep, X.rflags, X.rparams, R.final_G + g0);
+        // final cut of the group from its repaired spins, packed again
+        pack_kernel<<<pg, 256, 0, st>>>(spins, N, g0, nrep, X.packed);
+        cudaMemsetAsync(R.final_cut + g0, 0, nrep * sizeof(int64_t), st);
+        packed_cut_kernel<<<nb, 256, 0, st>>>(P, X.packed, nrep, R.final_cut + g0);
+    }
     return (int)cudaGetLastError();
 }
 

@@ -2,6 +2,7 @@
 // (gdi_kernels.cu) of libgdi.so.  Not part of the public ABI.
 #pragma once
 
+#include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
 
@@ -85,9 +86,15 @@ int gdi_grid_plan(const GdiDevProblem &P, int max_row, int sms, size_t smem_limi
 // cost_off[c]); every block gets at most wpc windows.  bnd has num_classes * (blocks + 1) entries.
 void gdi_grid_window_bounds(const int64_t *cost, const int64_t *cost_off, int num_classes, int blocks,
                             int wpc, int32_t *bnd);
+// Event pairs recorded around every anneal kernel launch (timing of the kernel alone).
+struct GdiKernelTimer {
+    cudaEvent_t *ev;                 // [2 * cap] begin/end events, or null (not timed)
+    int cap;                         // pairs available
+    int n;                           // pairs recorded
+};
 int gdi_launch_grid_anneal(const GdiDevProblem &P, const GdiDevRun &R, const GdiGridScratch &X,
                            int8_t *spins, int sms, int spc, int wpc, size_t smem, const int32_t *wbnd,
-                           void *stream);
+                           GdiKernelTimer *timer, void *stream);
 int gdi_launch_grid_finish(const GdiDevProblem &P, const GdiDevRun &R, const GdiGridScratch &X,
                            int8_t *spins, int do_repair, void *stream);
 int gdi_launch_gather_spins(const GdiDevProblem &P, const int8_t *spins_rank, int8_t *out_orig,

@@ -167,7 +167,7 @@ extern "C" int gdi_anneal_static(int32_t n, const int64_t *row_ptr, const uint32
     e = cudaMemsetAsync(X.err, 0, sizeof(int32_t), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(X.status, 0, 16 * sizeof(int32_t), st);
     if (e != cudaSuccess) return gdi_set_error(GDI_ERR_CUDA, std::string("gdi_anneal_static: ") + cudaGetErrorString(e));
-    const int ke = gdi_launch_grid_anneal(P, R, X, spins, nblk, spc, wpc, smem, nullptr, st);
+    const int ke = gdi_launch_grid_anneal(P, R, X, spins, nblk, spc, wpc, smem, nullptr, nullptr, st);
     if (ke) return gdi_set_error(GDI_ERR_CUDA, std::string("gdi_anneal_static launch: ") +
                                                    cudaGetErrorString((cudaError_t)ke));
     return GDI_OK;

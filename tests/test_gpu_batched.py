@@ -73,10 +73,39 @@ def test_cuda_graph_replay_equals_direct_anneal(gdi, grid_path):
     with torch.cuda.stream(stream):
         a.anneal(sch, 21, stream=stream)
     ref_spins, ref_cut = a.spins().copy(), a.results()["final_cut"].copy()
+    ms, n = a.kernel_ms()
+    assert ms > 0 and n == 1
     graph = a.capture_graph(sch, 21, stream)
+    with pytest.raises(gdi.GdiError):
+        a.kernel_ms()          # a captured anneal records no timing events
     for _ in range(2):
         graph.replay()
         torch.cuda.synchronize()
         assert np.array_equal(a.spins(), ref_spins)
         assert np.array_equal(a.results()["final_cut"], ref_cut)
     a.close()
+
+
+def test_kernel_time_counts_sweep_launches(gdi):
+    """The sweep kernel is timed alone: one launch per group of 8 replicas on the grid path, one on
+    the CTA path, each shorter than the whole anneal measured around it."""
+    import torch
+    g = barabasi_albert(30000, 5, 73)
+    a = gdi.Annealer(g, A=1, B=4, W=64, replicas=11)
+    a.configure(path=gdi.GDI_PATH_GRID)
+    sch = gdi.Schedule(sweeps=20, t0=12.0, t1=0.2)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    a.anneal(sch, 5, stream=torch.cuda.current_stream())
+    e1.record()
+    torch.cuda.synchronize()
+    ms, n = a.kernel_ms()
+    assert n == 2 and 0 < ms < e0.elapsed_time(e1)
+    a.configure(path=gdi.GDI_PATH_CTA)
+    small = barabasi_albert(3000, 4, 74)
+    b = gdi.Annealer(small, A=1, B=4, W=64, replicas=4)
+    b.anneal(sch, 5)
+    ms2, n2 = b.kernel_ms()
+    assert n2 == 1 and ms2 > 0
+    a.close()
+    b.close()
