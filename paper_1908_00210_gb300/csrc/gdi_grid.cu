@@ -935,32 +935,50 @@ __device__ __forceinline__ bool wait_exact(const unsigned long long *f, uint32_t
     return true;
 }
 
-// ascending bitonic sort of 32 * S keys held as key[s] of lane l = element l * S + s
+// ascending sort of 32 * S keys held as key[s] of lane l = element l * S + s: a bitonic network in
+// its all-ascending form (every merge starts with a "flip" stage that pairs element e with
+// e ^ (size - 1), then half-cleaners pair e with e ^ j), so that a compare-exchange always sends
+// the minimum to the lower element -- in-register steps are a plain min/max pair
 template <int S>
 __device__ __forceinline__ void warp_bitonic(uint32_t (&key)[S])
 {
     const int lane = threadIdx.x & 31;
 #pragma unroll
     for (int size = 2; size <= 32 * S; size <<= 1) {
+        if (size <= S) {
 #pragma unroll
-        for (int j = size >> 1; j >= 1; j >>= 1) {
+            for (int s = 0; s < S; ++s) {
+                if ((s & (size >> 1)) == 0) {
+                    const int q = s ^ (size - 1);
+                    const uint32_t a = key[s], b = key[q];
+                    key[s] = min(a, b);
+                    key[q] = max(a, b);
+                }
+            }
+        } else {
+            const bool lower = ((lane * S) & (size >> 1)) == 0;
+            uint32_t o[S];
+#pragma unroll
+            for (int s = 0; s < S; ++s) o[s] = __shfl_xor_sync(0xFFFFFFFFu, key[S - 1 - s], size / S - 1);
+#pragma unroll
+            for (int s = 0; s < S; ++s) key[s] = lower ? min(key[s], o[s]) : max(key[s], o[s]);
+        }
+#pragma unroll
+        for (int j = size >> 2; j >= 1; j >>= 1) {
             if (j >= S) {
+                const bool keep_min = ((lane * S) & j) == 0;
 #pragma unroll
                 for (int s = 0; s < S; ++s) {
                     const uint32_t o = __shfl_xor_sync(0xFFFFFFFFu, key[s], j / S);
-                    const int e = lane * S + s;
-                    const bool keep_min = ((e & j) == 0) == ((e & size) == 0);
                     key[s] = keep_min ? min(key[s], o) : max(key[s], o);
                 }
             } else {
 #pragma unroll
                 for (int s = 0; s < S; ++s) {
                     if ((s & j) == 0) {
-                        const int e = lane * S + s;
                         const uint32_t a = key[s], b = key[s + j];
-                        const bool swap = ((e & size) == 0) ? (a > b) : (a < b);
-                        key[s] = swap ? b : a;
-                        key[s + j] = swap ? a : b;
+                        key[s] = min(a, b);
+                        key[s + j] = max(a, b);
                     }
                 }
             }
