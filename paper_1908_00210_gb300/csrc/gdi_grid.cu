@@ -1285,29 +1285,50 @@ __global__ void __launch_bounds__(GB, 1) gdi_grid_sorted_kernel(GridArgs A)
                     for (int kk = 0; kk < nwin; ++kk) {
                         const int ws = kk * W, we = min(ws + W, ns);
                         if (x >= -FAST_X && x <= FAST_X) {
+                            // members of the window in registers (slot s = positions ws + 32 s + lane)
+                            int32_t rv[SL];
+                            uint32_t ng = 0, vd = 0;            // bit s: member is -1 / exists
+#pragma unroll
+                            for (int s = 0; s < SL; ++s) {
+                                const int i = ws + 32 * s + lane;
+                                rv[s] = 0;
+                                if (i < we) {
+                                    rv[s] = rr[i];
+                                    vd |= 1u << s;
+                                    ng |= ((uint32_t)(s0[i] >> r) & 1u) << s;
+                                }
+                            }
+                            uint32_t wbits[SL];
+#pragma unroll
+                            for (int s = 0; s < SL; ++s) wbits[s] = 0;
 #pragma unroll
                             for (int ph = 0; ph < 2; ++ph) {
                                 const bool plus = plus_first == (ph == 0);
                                 int32_t cnt = 0;
-                                for (int q = ws; q < we; q += 32) {
-                                    const int i = q + lane;
-                                    bool f = false;
-                                    if (i < we) {
-                                        const bool neg = (s0[i] >> r) & 1;
-                                        if (neg != plus) {
-                                            const int32_t rv = rr[i];
-                                            f = plus ? rv <= x : rv >= x;
-                                        }
-                                    }
+#pragma unroll
+                                for (int s = 0; s < SL; ++s) {
+                                    const bool mem = ((vd >> s) & 1u) && (((ng >> s) & 1u) != (plus ? 1u : 0u));
+                                    const bool f = mem && (plus ? rv[s] <= x : rv[s] >= x);
                                     const unsigned bm = __ballot_sync(0xFFFFFFFFu, f);
                                     cnt += __popc(bm);
-                                    if (lane == 0 && bm) {
-                                        const int sh = q & 31;
-                                        fb[q >> 5] |= bm << sh;
-                                        if (sh) fb[(q >> 5) + 1] |= bm >> (32 - sh);
-                                    }
+                                    wbits[s] |= bm;
                                 }
                                 x = plus ? x - 2 * cnt : x + 2 * cnt;
+                            }
+                            // flip words: slot s covers positions [ws + 32 s, ws + 32 s + 32)
+                            if ((ws & 31) == 0) {
+#pragma unroll
+                                for (int s = 0; s < SL; ++s)
+                                    if (lane == s && ws + 32 * s < we) fb[(ws >> 5) + s] = wbits[s];
+                            } else if (lane == 0) {
+                                const int sh = ws & 31;
+#pragma unroll
+                                for (int s = 0; s < SL; ++s) {
+                                    if (!wbits[s]) continue;
+                                    const int q = (ws >> 5) + s;
+                                    fb[q] |= wbits[s] << sh;
+                                    fb[q + 1] |= wbits[s] >> (32 - sh);
+                                }
                             }
                         } else {
                             x = window_replay_exact(gr, s0, r, ws, we, c0 + x, plus_first, bins, fm) - c0;
