@@ -189,34 +189,32 @@ __device__ __forceinline__ void field8_thread(const GdiDevProblem &P, int64_t ba
     }
 }
 
-// Partial sums of one chunk [c0, c1) of a long row, by one warp: sw = sum of weights,
-// sb[k] = sum of w * bit_k (bit_k set = replica k is -1); valid in every lane.
+// Partial sums of one chunk [c0, c1) of a long row (c1 - c0 <= LCHUNK), by one warp: sw = sum of
+// weights, sb[k] = sum of w * bit_k (bit_k set = replica k is -1); valid in every lane.  Lanes take
+// entries c0 + lane + 32 t in predicated batches of 8 (every load of a batch in flight at once).
+constexpr int LCHUNK = 512;
 __device__ __forceinline__ void chunk8_warp(const GdiDevProblem &P, int64_t base, int64_t c0, int64_t c1,
                             const uint8_t *packed, int32_t &sw, int32_t sb[8])
 {
     const int lane = threadIdx.x & 31;
     uint64_t aP = 0, aN = 0;
     int32_t nN = 0, n = 0;
-    // at most ceil(1024 / 32) = 32 entries per lane: byte lanes cannot overflow
-    int64_t e = c0 + lane;
-    for (; e + 96 < c1; e += 128) {
-        const uint32_t x0 = __ldg(P.col + e), x1 = __ldg(P.col + e + 32);
-        const uint32_t x2 = __ldg(P.col + e + 64), x3 = __ldg(P.col + e + 96);
-        const uint64_t s0 = spread8(__ldcg(packed + base + (x0 & 0x7FFFFFFFu)));
-        const uint64_t s1 = spread8(__ldcg(packed + base + (x1 & 0x7FFFFFFFu)));
-        const uint64_t s2 = spread8(__ldcg(packed + base + (x2 & 0x7FFFFFFFu)));
-        const uint64_t s3 = spread8(__ldcg(packed + base + (x3 & 0x7FFFFFFFu)));
-        if (x0 >> 31) { aN += s0; ++nN; } else aP += s0;
-        if (x1 >> 31) { aN += s1; ++nN; } else aP += s1;
-        if (x2 >> 31) { aN += s2; ++nN; } else aP += s2;
-        if (x3 >> 31) { aN += s3; ++nN; } else aP += s3;
-        n += 4;
-    }
-    for (; e < c1; e += 32) {
-        const uint32_t x = __ldg(P.col + e);
-        const uint64_t sv = spread8(__ldcg(packed + base + (x & 0x7FFFFFFFu)));
-        if (x >> 31) { aN += sv; ++nN; } else aP += sv;
-        ++n;
+    // at most LCHUNK / 32 = 16 entries per lane: byte lanes cannot overflow
+    for (int64_t e0 = c0 + lane; e0 < c1; e0 += 32 * 8) {
+        uint32_t x[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) x[k] = e0 + 32 * k < c1 ? __ldg(P.col + e0 + 32 * k) : 0u;
+        uint8_t b[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            b[k] = e0 + 32 * k < c1 ? __ldcg(packed + base + (x[k] & 0x7FFFFFFFu)) : (uint8_t)0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            if (e0 + 32 * k >= c1) continue;
+            const uint64_t sv = spread8(b[k]);
+            if (x[k] >> 31) { aN += sv; ++nN; } else aP += sv;
+            ++n;
+        }
     }
     sw = warp_sum(n - 2 * nN);
 #pragma unroll
@@ -449,7 +447,7 @@ __device__ void range_thresholds(const GridArgs &A, const GSmem &S, int32_t a0, 
     }
     __syncthreads();
     if (all_reps) {
-        // long rows: chunks of 1024 entries are warp tasks; partial sums meet in shared memory.
+        // long rows: chunks of LCHUNK entries are warp tasks; partial sums meet in shared memory.
         // acc[i*8 + k] = sum_j w_ij bit_k(j) lives in the threshold array (free until the
         // thresholds are written below); sum_j w_ij lives in the first 4 bytes of the row's
         // field slots; the chunk count of long row t is kept in the histogram area.
@@ -459,7 +457,7 @@ __device__ void range_thresholds(const GridArgs &A, const GSmem &S, int32_t a0, 
         for (int t = threadIdx.x; t < nl; t += GB) {
             const int32_t i = S.longq[t];
             const int64_t deg = P.row_ptr[base + a0 + i + 1] - P.row_ptr[base + a0 + i];
-            nchunk[t] = (int32_t)((deg + 1023) / 1024);
+            nchunk[t] = (int32_t)((deg + LCHUNK - 1) / LCHUNK);
 #pragma unroll
             for (int k = 0; k < 8; ++k) acc[(size_t)i * 8 + k] = 0;
             *reinterpret_cast<int32_t *>(hbuf + (size_t)i * 8) = 0;
@@ -473,7 +471,7 @@ __device__ void range_thresholds(const GridArgs &A, const GSmem &S, int32_t a0, 
                     if (task % NWARP != warp_id()) continue;
                     const int32_t i = S.longq[t];
                     const int64_t r0 = P.row_ptr[base + a0 + i], r1 = P.row_ptr[base + a0 + i + 1];
-                    const int64_t c0 = r0 + (int64_t)c * 1024, c1 = min(r1, c0 + 1024);
+                    const int64_t c0 = r0 + (int64_t)c * LCHUNK, c1 = min(r1, c0 + LCHUNK);
                     int32_t swv, sb[8];
                     chunk8_warp(P, base, c0, c1, packed, swv, sb);
                     if ((threadIdx.x & 31) == 0) {
