@@ -57,6 +57,7 @@ class _Params(C.Structure):
         ("first_sweep", C.c_int32),
         ("last_sweep", C.c_int32),
         ("check_invariants", C.c_int32),
+        ("first_replica", C.c_int32),
     ]
 
 
@@ -172,8 +173,9 @@ def anneal(g, *, A: int = 1, B: int = 1, W: int = 0, mode: int = METROPOLIS, t0:
            t1: float = 0.05, pf0: float = 0.2, pf1: float = 0.01, sweeps: int = 100,
            seed: int = 1, instance: int = 0, replicas: int = 1, color=None, init=None,
            first_sweep: int = 0, last_sweep: int = 0, trace: bool = True,
-           check_invariants: bool = False, repair: bool = True) -> AnnealResult:
-    """Run the oracle annealer on one instance (all replicas)."""
+           check_invariants: bool = False, repair: bool = True, first_replica: int = 0) -> AnnealResult:
+    """Run the oracle annealer on one instance: replicas first_replica .. first_replica + replicas - 1
+    (output row k is replica first_replica + k)."""
     n = g.n
     rp = np.ascontiguousarray(g.row_ptr, dtype=np.int64)
     cc = np.ascontiguousarray(g.col, dtype=np.int32)
@@ -191,7 +193,7 @@ def anneal(g, *, A: int = 1, B: int = 1, W: int = 0, mode: int = METROPOLIS, t0:
     ctr = np.zeros((replicas, sweeps), dtype=np.int64) if trace else None
     P = _Params(n, _p(rp), _p(cc), _p(ww), _p(colr), A, B, W, mode, t0, t1, pf0, pf1, sweeps,
                 seed & 0xFFFFFFFFFFFFFFFF, instance, replicas, first_sweep, last_sweep,
-                1 if check_invariants else 0)
+                1 if check_invariants else 0, first_replica)
     O = _Out(_p(spins), 1 if init is not None else 0, _p(raw_G), _p(final_G), _p(raw_cut),
              _p(final_cut), _p(dig), _p(gtr), _p(ctr), 0, 0, 1 if repair else 0)
     rc = lib().oracle_anneal(C.byref(P), C.byref(O))
@@ -199,3 +201,18 @@ def anneal(g, *, A: int = 1, B: int = 1, W: int = 0, mode: int = METROPOLIS, t0:
         raise ValueError(f"oracle_anneal failed with code {rc}")
     return AnnealResult(spins, raw_G, final_G, raw_cut, final_cut, dig, gtr, ctr,
                         int(O.invariant_failures), int(O.num_colors))
+
+
+def _anneal_job(args):
+    g, kw = args
+    return anneal(g, **kw)
+
+
+def anneal_parallel(g, *, replica_ids, processes: int = 8, **kw):
+    """oracle.anneal for the replicas in replica_ids, one replica per task on a pool of `processes`
+    spawned workers (never forked: the caller may already hold a GPU context).  Returns a list of
+    AnnealResult, one per replica id, each with a single row."""
+    import multiprocessing as mp
+    jobs = [(g, dict(kw, replicas=1, first_replica=int(r))) for r in replica_ids]
+    with mp.get_context("spawn").Pool(min(processes, len(jobs))) as pool:
+        return pool.map(_anneal_job, jobs)

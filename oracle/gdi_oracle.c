@@ -278,6 +278,7 @@ typedef struct {
     int32_t first_sweep;       /* resume support: anneal sweeps [first_sweep, sweeps) */
     int32_t last_sweep;        /* exclusive end; <= 0 means sweeps */
     int32_t check_invariants;  /* recompute G and cut after every window */
+    int32_t first_replica;     /* replica index of output row 0 (Philox counter word 3, digest) */
 } oracle_params;
 
 typedef struct {
@@ -448,7 +449,7 @@ int oracle_anneal(const oracle_params *p, oracle_out *o)
         } else {
             for (int32_t pr = 0; 2 * pr + 1 < n; ++pr) {
                 const uint32_t u = draw_word(p->seed, (uint32_t)(pr >> 2), 0xFFFFFFFFu,
-                                             (uint32_t)p->instance, (uint32_t)rep, pr & 3);
+                                             (uint32_t)p->instance, (uint32_t)(p->first_replica + rep), pr & 3);
                 const int8_t a = (u >> 31) ? -1 : 1;
                 s[2 * pr] = a;
                 s[2 * pr + 1] = (int8_t)-a;
@@ -476,7 +477,7 @@ int oracle_anneal(const oracle_params *p, oracle_out *o)
                             h += weight_of(p, e) * s[rank[p->col[e]]];
                         hbuf[r] = h;
                         const uint32_t u = draw_word(p->seed, (uint32_t)(r >> 2), (uint32_t)sw,
-                                                     (uint32_t)p->instance, (uint32_t)rep, r & 3);
+                                                     (uint32_t)p->instance, (uint32_t)(p->first_replica + rep), r & 3);
                         const int64_t Es = estar(row, ecap, u);
                         gbuf[r] = (s[r] > 0) ? gamma_plus(h, Es, p->A, p->B)
                                              : gamma_minus(h, Es, p->A, p->B);
@@ -517,7 +518,7 @@ int oracle_anneal(const oracle_params *p, oracle_out *o)
                 if (o->digest) {
                     uint64_t d = 0;
                     for (int32_t r = 0; r < n; ++r)
-                        if (s[r] > 0) d += digest_term(r, sw, rep);
+                        if (s[r] > 0) d += digest_term(r, sw, p->first_replica + rep);
                     o->digest[idx] = d;
                 }
                 if (o->G_trace) o->G_trace[idx] = (int32_t)G;

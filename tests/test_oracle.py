@@ -380,3 +380,12 @@ def test_anneal_reaches_bruteforce_optimum():
         assert r.final_cut[0] >= best
         hits += int(r.final_cut[0] == best)
     assert hits >= 29
+
+
+def test_replica_offset_selects_the_same_streams():
+    """first_replica only renames rows: replicas 2, 3 run alone equal rows 2, 3 of a 4-replica run."""
+    g = erdos_renyi(300, 0.05, 3)
+    a = oracle.anneal(g, A=1, B=4, W=16, sweeps=20, t0=12.0, t1=0.2, seed=5, replicas=4)
+    b = oracle.anneal(g, A=1, B=4, W=16, sweeps=20, t0=12.0, t1=0.2, seed=5, replicas=2, first_replica=2)
+    assert np.array_equal(a.spins[2:], b.spins) and np.array_equal(a.digest[2:], b.digest)
+    assert np.array_equal(a.final_cut[2:], b.final_cut) and np.array_equal(a.G_trace[2:], b.G_trace)
