@@ -211,8 +211,8 @@ class MPNN:
                                 self.v.data_ptr(), self.params_bf16.data_ptr(), self.lr, beta1, beta2, eps, self.step,
                                 self._st()), "adam")
 
-    def train_step(self, b: GraphBatch, y):
-        z, cache = self.forward(b)
+    def train_step(self, b: GraphBatch, y, X=None):
+        z, cache = self.forward(b, X)
         loss, _ = self.loss_and_backward(b, y, z, cache)
         self.adam()
         return loss
@@ -245,6 +245,77 @@ def make_graphs(count: int, seed0: int, n_lo=1000, n_hi=5000):
     return out
 
 
+def _graph_chunk(args):
+    count, seed0, n_lo, n_hi = args
+    return make_graphs(count, seed0, n_lo, n_hi)
+
+
+def make_graphs_parallel(count: int, seed0: int, n_lo=1000, n_hi=5000, processes=16, chunk=256):
+    """make_graphs in spawned worker processes (same graphs, same order); the graph of index i
+    always comes from seed seed0 + i, so chunks keep the ER / RGG alternation only if `chunk` is
+    even."""
+    import multiprocessing as mp
+    jobs = [(min(chunk, count - i), seed0 + i, n_lo, n_hi) for i in range(0, count, chunk)]
+    with mp.get_context("spawn").Pool(processes) as pool:
+        parts = pool.map(_graph_chunk, jobs)
+    return [g for part in parts for g in part]
+
+
+class Dataset:
+    """Training graphs resident on the device as one disjoint union (CSR, features, labels), cut
+    into batches of `batch` consecutive graphs without copying the graphs themselves."""
+
+    def __init__(self, graphs, labels, model, batch=16, chunk=2048):
+        import torch
+        from gdi_synth import batch_union
+        self.graphs = graphs
+        gp, u = batch_union(graphs)
+        self.gp = gp
+        self.row_ptr_h = u.row_ptr
+        self.row_ptr = torch.from_numpy(u.row_ptr).cuda()
+        self.col = torch.from_numpy(u.col).cuda()
+        self.y = torch.from_numpy(np.asarray(labels, dtype=np.int8)).cuda()
+        self.X = torch.empty((int(gp[-1]), FIN), dtype=torch.float32, device="cuda")
+        for g0 in range(0, len(graphs), chunk):      # features of every graph, once
+            g1 = min(len(graphs), g0 + chunk)
+            b = self.batch(g0, g1, with_x=False)
+            self.X[int(gp[g0]):int(gp[g1])] = model.features(b)
+        self.bsize = batch
+
+    def batch(self, g0, g1, with_x=True):
+        import torch
+        v0, v1 = int(self.gp[g0]), int(self.gp[g1])
+        e0, e1 = int(self.row_ptr_h[v0]), int(self.row_ptr_h[v1])
+        b = GraphBatch(N=v1 - v0, G=g1 - g0, max_n=int(max(g.n for g in self.graphs[g0:g1])),
+                       graph_ptr_h=self.gp[g0:g1 + 1] - v0,
+                       row_ptr=(self.row_ptr[v0:v1 + 1] - e0).contiguous(),
+                       col=(self.col[e0:e1] - v0).contiguous(),
+                       graph_ptr=torch.from_numpy(self.gp[g0:g1 + 1] - v0).cuda(),
+                       graph_id=torch.from_numpy(np.arange(g0, g1, dtype=np.int32)).cuda(),
+                       graphs=self.graphs[g0:g1])
+        return (b, self.X[v0:v1], self.y[v0:v1]) if with_x else b
+
+
+def train_dataset(model: MPNN, ds: Dataset, *, epochs=10, seed=0, log=None):
+    """Adam over the dataset's batches (consecutive groups of graphs, visited in a new random
+    order every epoch)."""
+    rng = np.random.default_rng(seed)
+    starts = np.arange(0, len(ds.graphs), ds.bsize)
+    history = []
+    for ep in range(epochs):
+        rng.shuffle(starts)
+        tot = 0.0
+        for g0 in starts:
+            g1 = min(len(ds.graphs), g0 + ds.bsize)
+            b, X, y = ds.batch(int(g0), int(g1))
+            loss = model.train_step(b, y, X)
+            tot += float(loss.item()) * (g1 - g0)
+        history.append(tot / len(ds.graphs))
+        if log:
+            log(f"epoch {ep}: loss {history[-1]:.4f}")
+    return history
+
+
 def anneal_batch(graphs, *, sweeps, t0, t1, seed, replicas, init=None, A=1, Bc=4, W=256, stream=None):
     """Random-start (or given-start) anneal of every graph; returns (final_cut [G, R], spins [R, N],
     GPU milliseconds of the anneal kernel launch sequence)."""
@@ -269,16 +340,22 @@ def anneal_batch(graphs, *, sweeps, t0, t1, seed, replicas, init=None, A=1, Bc=4
     return cut, spins, ms
 
 
-def label_graphs(graphs, *, sweeps=2000, replicas=4, seed=1):
-    """Labels = the best (lowest repaired cut) of `replicas` plain random-start anneals."""
-    cut, spins, _ = anneal_batch(graphs, sweeps=sweeps, t0=3.0, t1=0.05, seed=seed, replicas=replicas)
-    from gdi_synth import batch_union
-    gp, _ = batch_union(graphs)
-    y = np.empty(gp[-1], dtype=np.int8)
-    for g in range(len(graphs)):
-        best = int(np.argmin(cut[g]))
-        y[gp[g]:gp[g + 1]] = spins[best, gp[g]:gp[g + 1]]
-    return y, cut.min(axis=1)
+def label_graphs(graphs, *, sweeps=2000, replicas=4, seed=1, chunk=2048):
+    """Labels = the best (lowest repaired cut) of `replicas` plain random-start anneals, annealed
+    `chunk` graphs per batched launch."""
+    ys, bests = [], []
+    for g0 in range(0, len(graphs), chunk):
+        part = graphs[g0:g0 + chunk]
+        cut, spins, _ = anneal_batch(part, sweeps=sweeps, t0=3.0, t1=0.05, seed=seed, replicas=replicas)
+        from gdi_synth import batch_union
+        gp, _ = batch_union(part)
+        y = np.empty(gp[-1], dtype=np.int8)
+        for g in range(len(part)):
+            best = int(np.argmin(cut[g]))
+            y[gp[g]:gp[g + 1]] = spins[best, gp[g]:gp[g + 1]]
+        ys.append(y)
+        bests.append(cut.min(axis=1))
+    return np.concatenate(ys), np.concatenate(bests)
 
 
 def train(model: MPNN, graphs, labels, *, epochs=30, batch=16, seed=0, log=None):
@@ -369,20 +446,27 @@ def main():
     ap.add_argument("--lam", type=float, default=0.1)
     ap.add_argument("--t-low", type=float, default=0.5)
     ap.add_argument("--out", default="")
+    ap.add_argument("--processes", type=int, default=16, help="host processes generating the graphs")
     args = ap.parse_args()
-    import torch
-    torch.cuda.set_device(0)
     log = lambda s: print(s, flush=True)  # noqa: E731
     t0 = time.time()
-    train_graphs = make_graphs(args.train, 500_000)
-    test_graphs = make_graphs(args.test, 900_000)
+    train_graphs = make_graphs_parallel(args.train, 500_000, processes=args.processes)
+    test_graphs = make_graphs_parallel(args.test, 900_000, processes=args.processes)
     log(f"graphs generated in {time.time() - t0:.1f} s")
+    import torch
+    torch.cuda.set_device(0)
     t0 = time.time()
     labels, best = label_graphs(train_graphs, sweeps=args.label_sweeps)
+    torch.cuda.synchronize()
     log(f"labels in {time.time() - t0:.1f} s")
     model = MPNN(seed=0, lr=args.lr, lam=args.lam, steps=args.steps)
     t0 = time.time()
-    hist = train(model, train_graphs, labels, epochs=args.epochs, log=log)
+    ds = Dataset(train_graphs, labels, model)
+    torch.cuda.synchronize()
+    log(f"features of the training graphs in {time.time() - t0:.1f} s")
+    t0 = time.time()
+    hist = train_dataset(model, ds, epochs=args.epochs, log=log)
+    torch.cuda.synchronize()
     log(f"trained in {time.time() - t0:.1f} s")
     res = evaluate(model, test_graphs, log=log, t_low=args.t_low)
     res["train_loss"] = hist
