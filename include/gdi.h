@@ -54,7 +54,8 @@ extern "C" {
 /* kernel paths (gdi_configure) */
 #define GDI_PATH_AUTO 0   /* CTA-resident unless a single instance has more than 32768 vertices  */
 #define GDI_PATH_CTA  1   /* one thread block anneals one (instance, replica), spins in shared memory */
-#define GDI_PATH_GRID 2   /* one instance over every SM (needs W >= 1); up to 8 replicas per pass  */
+#define GDI_PATH_GRID 2   /* one instance over every SM (needs W >= 1); up to 8 replicas per pass;
+                             W <= 256: sorted-window kernel, W > 256: tabulated-window kernel */
 
 /* gdi_run.flags */
 #define GDI_FLAG_TRACE     1  /* record per-sweep G, cut and state digest (slower; for parity)     */
@@ -155,7 +156,9 @@ int gdi_autotune(gdi_ctx *ctx, const gdi_schedule *schedule, int32_t probe_sweep
                  int32_t *block_out, int32_t *grid_out, float *ms_out);
 
 /* What the last gdi_anneal launched: path, blocks, dynamic shared memory per block, and how many
- * times the grid-scale path took its exact fallback (0 on the CTA path).  Synchronises. */
+ * times the grid-scale path took its exact fallback -- a block whose G-map could not carry the
+ * running magnetisation and replayed its windows exactly instead (0 on the CTA path; a count of
+ * events, summed over replicas).  Synchronises. */
 int gdi_last_launch(gdi_ctx *ctx, int32_t *path, int32_t *grid, int64_t *smem_bytes,
                     int32_t *fallbacks);
 
