@@ -162,6 +162,16 @@ int gdi_autotune(gdi_ctx *ctx, const gdi_schedule *schedule, int32_t probe_sweep
 int gdi_last_launch(gdi_ctx *ctx, int32_t *path, int32_t *grid, int64_t *smem_bytes,
                     int32_t *fallbacks);
 
+/* Failure-detection test hook (the paper has no counterpart).  The next gdi_anneal that takes the
+ * grid-scale path starts with its grid barrier's arrival counter already past the trigger, set
+ * from the host, so no barrier can complete -- a flag that no block will ever set.  Every block's
+ * bounded wait then gives up after spin_limit polls (>= 1; each poll sleeps tens of ns), sets the
+ * device error word and returns; the anneal reports GDI_ERR_TIMEOUT (from gdi_get_results and
+ * the other synchronising calls).  Nothing faults, traps or hangs, the context stays usable, and
+ * the following anneal runs normally.  The CTA-resident path has no cross-block waits and ignores
+ * the hook, which stays armed until a grid-scale anneal consumes it. */
+int gdi_inject_wait_failure(gdi_ctx *ctx, int64_t spin_limit);
+
 /* Device time of the anneal kernel launches of the last gdi_anneal (the sweep kernels alone,
  * without the initialisation, packing, cut and repair kernels around them), measured with CUDA
  * events recorded on the anneal's stream around every launch: *ms = their sum, *launches = how

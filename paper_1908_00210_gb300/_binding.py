@@ -27,7 +27,8 @@ ERRORS = {
 # every entry point that include/gdi.h declares
 EXPORTS = ["gdi_create", "gdi_anneal", "gdi_get_spins", "gdi_get_results", "gdi_cut", "gdi_balance",
            "gdi_get_trace", "gdi_configure", "gdi_last_launch", "gdi_info", "gdi_destroy",
-           "gdi_strerror", "gdi_last_error", "gdi_anneal_static", "gdi_autotune", "gdi_kernel_time"]
+           "gdi_strerror", "gdi_last_error", "gdi_anneal_static", "gdi_autotune", "gdi_kernel_time",
+           "gdi_inject_wait_failure"]
 GDI_PATH_AUTO, GDI_PATH_CTA, GDI_PATH_GRID = 0, 1, 2
 
 
@@ -84,6 +85,7 @@ def load():
                                     i32, i32, i32, i32, C.c_uint64, i32, vp, vp, vp]
     L.gdi_last_launch.argtypes = [vp, vp, vp, vp, vp]
     L.gdi_kernel_time.argtypes = [vp, vp, vp]
+    L.gdi_inject_wait_failure.argtypes = [vp, C.c_int64]
     L.gdi_destroy.argtypes = [vp]
     L.gdi_destroy.restype = None
     L.gdi_strerror.argtypes = [C.c_int]
@@ -248,6 +250,10 @@ class Annealer:
         fb = np.zeros(1, np.int32)
         _check(load().gdi_last_launch(self._h, pa.ctypes.data, gr.ctypes.data, sm.ctypes.data, fb.ctypes.data))
         return dict(path=int(pa[0]), grid=int(gr[0]), smem=int(sm[0]), fallbacks=int(fb[0]))
+
+    def inject_wait_failure(self, spin_limit: int = 1 << 16):
+        """Make the next grid-scale anneal's device waits run out (test of failure detection)."""
+        _check(load().gdi_inject_wait_failure(self._h, int(spin_limit)))
 
     def kernel_ms(self):
         """Device time (ms) of the last anneal's sweep-kernel launches and their number."""

@@ -87,6 +87,8 @@ struct gdi_ctx {
     // events around the anneal kernel launches of the last gdi_anneal (none while capturing)
     std::vector<cudaEvent_t> kev;
     int kev_pairs = 0;
+    // failure-detection test hook for the next grid-scale anneal (gdi_inject_wait_failure)
+    long long inject_limit = 0;
     std::vector<int32_t> num_classes;       // per instance
     DevBuf<int64_t> node_off, row_ptr;
     DevBuf<int32_t> class_off, class_ptr, rank_of;
@@ -170,6 +172,8 @@ struct gdi_ctx {
         X.rflags = g_rflags.p;
         X.rties = g_rties.p;
         X.rparams = g_rparams.p;
+        X.spin_limit = 1ll << 26;
+        X.bar_start = 0;
         return X;
     }
 };
@@ -694,7 +698,12 @@ int gdi_anneal(gdi_ctx *c, const gdi_schedule *S, const gdi_run *run)
         if (e != cudaSuccess) return fail(GDI_ERR_OOM, "device allocation failed (grid scratch)");
         cudaMemsetAsync(c->g_err.p, 0, sizeof(int32_t), st);
         cudaMemsetAsync(c->g_status.p, 0, 16 * sizeof(int32_t), st);
-        const GdiGridScratch X = c->grid_scratch();
+        GdiGridScratch X = c->grid_scratch();
+        if (c->inject_limit > 0) {               // no barrier can complete: every wait runs out
+            X.spin_limit = c->inject_limit;
+            X.bar_start = (unsigned int)nblk;
+            c->inject_limit = 0;
+        }
         const int32_t *wbnd = nullptr;
         if (c->W <= 256 && !c->wcost_off.empty()) {
             if (c->wbnd_blocks != nblk || c->wbnd_wpc != wpc) {
@@ -912,6 +921,13 @@ int gdi_last_launch(gdi_ctx *c, int32_t *path, int32_t *grid, int64_t *smem_byte
             for (int i = 0; i < 8; ++i) *fallbacks += st[i];
         }
     }
+    return GDI_OK;
+}
+
+int gdi_inject_wait_failure(gdi_ctx *c, int64_t spin_limit)
+{
+    if (!c || spin_limit < 1) return fail(GDI_ERR_INVALID_ARG, "need a context and spin_limit >= 1");
+    c->inject_limit = spin_limit;
     return GDI_OK;
 }
 

@@ -46,7 +46,6 @@ constexpr int HB = 2 * RT + 4 * KC + 1; // histogram bins for building a window 
 constexpr int HA = 2 * KC + 1;          // histogram bins for the exact apply
 constexpr int16_t TINV = INT16_MIN;
 constexpr int LONG_ROW = 48;
-constexpr long long SPIN_LIMIT = 1ll << 26;
 
 __device__ __forceinline__ int warp_id() { return threadIdx.x >> 5; }
 
@@ -115,7 +114,7 @@ __device__ bool grid_sync(const GdiGridScratch &X)
         } else {
             long long spins = 0;
             while (*gen == g0) {
-                if (++spins > SPIN_LIMIT) {
+                if (++spins > X.spin_limit) {
                     atomicExch(X.err, GDI_DEVERR_TIMEOUT);
                     good = 0;
                     break;
@@ -917,7 +916,7 @@ __device__ __forceinline__ void st_release_u64(unsigned long long *p, unsigned l
     asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-// bounded wait for an exact G word of this epoch: false (error word set) after SPIN_LIMIT polls
+// bounded wait for an exact G word of this epoch: false (error word set) after X.spin_limit polls
 // or when another block failed
 __device__ __forceinline__ bool wait_exact(const unsigned long long *f, uint32_t epoch, const GdiGridScratch &X,
                                            int32_t &g)
@@ -925,7 +924,7 @@ __device__ __forceinline__ bool wait_exact(const unsigned long long *f, uint32_t
     long long spins = 0;
     unsigned long long v;
     while (((v = ld_acquire_u64(f)) >> 32) != epoch) {
-        if (++spins > SPIN_LIMIT) { atomicExch(X.err, GDI_DEVERR_TIMEOUT); return false; }
+        if (++spins > X.spin_limit) { atomicExch(X.err, GDI_DEVERR_TIMEOUT); return false; }
         if ((spins & 63) == 0 && *(volatile int *)X.err) return false;
         __nanosleep(32);
     }
@@ -1083,7 +1082,7 @@ __device__ __forceinline__ bool poll_flags(const uint32_t *f, int cnt, uint32_t 
     if (lane < cnt) {
         long long spins = 0;
         while (ld_relaxed_u32(f + lane) != want) {
-            if (++spins > SPIN_LIMIT) { atomicExch(X.err, GDI_DEVERR_TIMEOUT); ok = false; break; }
+            if (++spins > X.spin_limit) { atomicExch(X.err, GDI_DEVERR_TIMEOUT); ok = false; break; }
             if ((spins & 63) == 0 && *(volatile int *)X.err) { ok = false; break; }
             __nanosleep(20);
         }
@@ -1359,6 +1358,8 @@ __global__ void __launch_bounds__(GB, 1) gdi_grid_sorted_kernel(GridArgs A)
         }
     }
 }
+
+__global__ void set_word_kernel(unsigned int *p, unsigned int v) { *p = v; }
 
 // ---------------------------------------------------------------------------------------------
 // replica group <-> int8 spins in rank space
@@ -1646,6 +1647,7 @@ int gdi_launch_grid_anneal(const GdiDevProblem &P, const GdiDevRun &R, const Gdi
         pack_kernel<<<pg, 256, 0, st>>>(spins, P.N, g0, nrep, X.packed);
         cudaMemsetAsync(X.Gcls, 0, 8 * sizeof(int32_t), st);
         cudaMemsetAsync(X.bar, 0, 2 * sizeof(unsigned int), st);
+        if (X.bar_start) set_word_kernel<<<1, 1, 0, st>>>(X.bar, X.bar_start);
         if (sorted) cudaMemsetAsync(X.tables, 0, chain_off_tab(sms), st);
         GridArgs A;
         A.P = P;

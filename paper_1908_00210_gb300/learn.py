@@ -340,13 +340,13 @@ def anneal_batch(graphs, *, sweeps, t0, t1, seed, replicas, init=None, A=1, Bc=4
     return cut, spins, ms
 
 
-def label_graphs(graphs, *, sweeps=2000, replicas=4, seed=1, chunk=2048):
+def label_graphs(graphs, *, sweeps=2000, replicas=4, seed=1, chunk=2048, A=1):
     """Labels = the best (lowest repaired cut) of `replicas` plain random-start anneals, annealed
     `chunk` graphs per batched launch."""
     ys, bests = [], []
     for g0 in range(0, len(graphs), chunk):
         part = graphs[g0:g0 + chunk]
-        cut, spins, _ = anneal_batch(part, sweeps=sweeps, t0=3.0, t1=0.05, seed=seed, replicas=replicas)
+        cut, spins, _ = anneal_batch(part, sweeps=sweeps, t0=3.0, t1=0.05, seed=seed, replicas=replicas, A=A)
         from gdi_synth import batch_union
         gp, _ = batch_union(part)
         y = np.empty(gp[-1], dtype=np.int8)
@@ -435,6 +435,88 @@ def evaluate(model: MPNN, graphs, *, seeds=8, full_sweeps=2000, ladder=LADDER, t
     return out
 
 
+def evaluate_many(starts, graphs, *, seeds=8, full_sweeps=2000, ladder=LADDER, A=1, log=None):
+    """Like evaluate, for several learned starts at once: starts = {name: (model, t_low)}.  The
+    target, the plain annealer's ladder (random start, T0 = 3.0) and a random-start control at every
+    t_low are computed once."""
+    import torch
+    ref_cut, _, full_ms = anneal_batch(graphs, sweeps=full_sweeps, t0=3.0, t1=0.05, seed=101, replicas=seeds, A=A)
+    c_ref = np.median(ref_cut, axis=1)
+    ns = np.array([g.n for g in graphs], dtype=np.float64)
+    share = ns / ns.sum()
+    out = {"c_ref_median": float(np.median(c_ref)), "full_random_ms": full_ms, "graphs": len(graphs),
+           "seeds": seeds, "ladder": ladder, "A": A}
+    methods = {"random_T3.0": dict(t0=3.0, init=None, infer=0.0)}
+    for t_low in sorted({t for _, t in starts.values()}):
+        methods[f"random_T{t_low}"] = dict(t0=t_low, init=None, infer=0.0)
+    for name, (model, t_low) in starts.items():
+        gb = GraphBatch.from_graphs(graphs, graph_ids=np.arange(len(graphs)) + 1_000_000)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        pred = model.predict_spins(gb)
+        e1.record()
+        torch.cuda.synchronize()
+        methods[name] = dict(t0=t_low, init=pred.repeat(seeds), infer=e0.elapsed_time(e1))
+    times = {}
+    for name, m in methods.items():
+        reached_at = np.full(len(graphs), -1)
+        rung_ms, rung_reached = {}, {}
+        for M in ladder:
+            cut, _, ms = anneal_batch(graphs, sweeps=M, t0=m["t0"], t1=0.05, seed=202, replicas=seeds,
+                                      init=m["init"], A=A)
+            rung_ms[M] = ms
+            med = np.median(cut, axis=1)
+            newly = (reached_at < 0) & (med <= c_ref)
+            reached_at[newly] = M
+            rung_reached[M] = int((reached_at > 0).sum())
+            if log:
+                log(f"{name} M={M}: reached {rung_reached[M]}/{len(graphs)} ({ms:.1f} ms)")
+        t = np.array([rung_ms[M] * share[g] if M > 0 else np.nan for g, M in enumerate(reached_at)])
+        t = t + m["infer"] * share
+        ok = reached_at > 0
+        times[name] = np.where(ok, t, np.nan)
+        out[name] = {"reached": rung_reached, "median_sweeps_to_cut": float(np.median(reached_at[ok])) if ok.any() else None,
+                     "median_gpu_ms_to_cut": float(np.median(t[ok])) if ok.any() else None,
+                     "infer_ms": m["infer"], "rung_ms": rung_ms}
+    for name in starts:
+        a, b = times[name], times["random_T3.0"]
+        both = np.isfinite(a) & np.isfinite(b)
+        out[name]["paired_vs_random_T3.0"] = {
+            "graphs_both_reached": int(both.sum()),
+            "median_time_ratio_random_over_learned": float(np.median(b[both] / a[both])) if both.any() else None,
+            "learned_faster_fraction": float(np.mean(a[both] < b[both])) if both.any() else None}
+    return out
+
+
+def ablate(args, log):
+    """One set of graphs and labels; a network per feature setting (diffusion steps), each
+    evaluated at every start temperature against one shared plain-annealer reference."""
+    import torch
+    t0 = time.time()
+    train_graphs = make_graphs_parallel(args.train, 500_000, processes=args.processes)
+    test_graphs = make_graphs_parallel(args.test, 900_000, processes=args.processes)
+    log(f"graphs generated in {time.time() - t0:.1f} s")
+    torch.cuda.set_device(0)
+    t0 = time.time()
+    labels, _ = label_graphs(train_graphs, sweeps=args.label_sweeps, A=args.A)
+    log(f"labels in {time.time() - t0:.1f} s")
+    starts, losses = {}, {}
+    for steps in [int(x) for x in args.ablate_steps.split(",")]:
+        model = MPNN(seed=0, lr=args.lr, lam=args.lam, steps=steps)
+        ds = Dataset(train_graphs, labels, model)
+        t0 = time.time()
+        losses[steps] = train_dataset(model, ds, epochs=args.epochs, log=log)
+        log(f"steps {steps}: trained in {time.time() - t0:.1f} s")
+        del ds
+        for t_low in [float(x) for x in args.ablate_t.split(",")]:
+            starts[f"learned_steps{steps}_T{t_low}"] = (model, t_low)
+    res = evaluate_many(starts, test_graphs, A=args.A, log=log)
+    res["train_loss"] = {str(k): v for k, v in losses.items()}
+    res["train_graphs"] = args.train
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--train", type=int, default=1024)
@@ -447,8 +529,18 @@ def main():
     ap.add_argument("--t-low", type=float, default=0.5)
     ap.add_argument("--out", default="")
     ap.add_argument("--processes", type=int, default=16, help="host processes generating the graphs")
+    ap.add_argument("--A", type=int, default=1, help="balance weight of the anneals (labels and evaluation)")
+    ap.add_argument("--ablate-steps", default="", help="comma list of diffusion steps: ablation mode")
+    ap.add_argument("--ablate-t", default="0.5", help="comma list of start temperatures (ablation mode)")
     args = ap.parse_args()
     log = lambda s: print(s, flush=True)  # noqa: E731
+    if args.ablate_steps:
+        res = ablate(args, log)
+        print(json.dumps({k: v for k, v in res.items() if k != "train_loss"}, default=str))
+        if args.out:
+            with open(args.out, "w") as f:
+                json.dump(res, f, default=str, indent=1)
+        return
     t0 = time.time()
     train_graphs = make_graphs_parallel(args.train, 500_000, processes=args.processes)
     test_graphs = make_graphs_parallel(args.test, 900_000, processes=args.processes)

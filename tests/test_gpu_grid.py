@@ -104,3 +104,24 @@ def test_grid_ba_1m_first_sweeps(gdi):
     on its first 2 sweeps (then repaired) against the oracle."""
     g = barabasi_albert(1_000_000, 5, 4004)
     grid_vs_oracle(gdi, g, W=256, sweeps=500, replicas=8, last_sweep=2, seed=1)
+
+
+def test_bounded_waits_report_timeout_and_context_recovers(gdi):
+    """Failure detection without a GPU fault: the host starts the grid barrier's arrival counter
+    past its trigger, so no block's wait can end; every wait gives up after a short bounded poll,
+    the anneal reports GDI_ERR_TIMEOUT, and the same context then anneals normally (bit-exact)."""
+    g = barabasi_albert(20000, 5, 60)
+    ann = gdi.Annealer(g, A=1, B=4, W=64, replicas=2)
+    ann.configure(path=gdi.GDI_PATH_GRID)
+    sch = gdi.Schedule(sweeps=6, t0=12.0, t1=0.2)
+    ann.inject_wait_failure(spin_limit=1 << 14)
+    ann.anneal(sch, 3)
+    with pytest.raises(gdi.GdiError) as err:
+        ann.results()
+    assert err.value.code == -9          # GDI_ERR_TIMEOUT
+    ann.anneal(sch, 3, flags=gdi.GDI_FLAG_TRACE)
+    res, spins = ann.results(), ann.spins()
+    ann.close()
+    ref = oracle.anneal(g, A=1, B=4, W=64, t0=12.0, t1=0.2, sweeps=6, seed=3, replicas=2)
+    assert np.array_equal(spins, ref.spins)
+    assert np.array_equal(res["final_cut"][0], ref.final_cut)
