@@ -1199,8 +1199,9 @@ __global__ void __launch_bounds__(GB, 1) gdi_grid_sorted_kernel(GridArgs A)
                 int8_t *dst = tabs + ((size_t)p * 8 + r) * NT;
                 dst[lane] = (int8_t)t0;
                 dst[lane + 32] = (int8_t)t1;
-                __threadfence();
             }
+            // the block barrier orders every warp's table stores before thread 0's release store,
+            // which publishes them at GPU scope (cumulative release)
             __syncthreads();
             if (threadIdx.x == 0) st_release_u32(flag + p, epoch);
             // ---- the last block of a run composes the run's block tables into the run table
@@ -1228,7 +1229,6 @@ __global__ void __launch_bounds__(GB, 1) gdi_grid_sorted_kernel(GridArgs A)
                         int8_t *rd = rtabs + ((size_t)run * 8 + r) * NT;
                         rd[lane] = (int8_t)u0;
                         rd[lane + 32] = (int8_t)u1;
-                        __threadfence();
                     }
                 }
                 __syncthreads();
