@@ -41,7 +41,7 @@ extern "C" {
 #define GDI_ERR_CUDA          -8   /* a CUDA runtime call failed (message in gdi_last_error)     */
 #define GDI_ERR_TIMEOUT       -9   /* a bounded device wait gave up; the context stays usable    */
 #define GDI_ERR_NOT_ANNEALED  -10  /* a getter was called before any gdi_anneal                  */
-#define GDI_ERR_TOO_LARGE     -11  /* no kernel variant supports this size in this build          */
+#define GDI_ERR_TOO_LARGE     -11  /* no kernel variant supports this size                        */
 
 /* memory kinds */
 #define GDI_MEM_HOST   0

@@ -981,7 +981,7 @@ const char *gdi_strerror(int code)
     case GDI_ERR_CUDA: return "CUDA error";
     case GDI_ERR_TIMEOUT: return "device wait timed out";
     case GDI_ERR_NOT_ANNEALED: return "no anneal has run";
-    case GDI_ERR_TOO_LARGE: return "problem too large for this build";
+    case GDI_ERR_TOO_LARGE: return "problem too large for the kernels";
     default: return "unknown error";
     }
 }
