@@ -61,6 +61,9 @@ extern "C" {
 #define GDI_FLAG_TRACE     1  /* record per-sweep G, cut and state digest (slower; for parity)     */
 #define GDI_FLAG_NO_REPAIR 2  /* skip the exact-balance repair after the last sweep                */
 #define GDI_FLAG_CONTINUE  4  /* start from the spins the previous gdi_anneal left (resume)        */
+#define GDI_FLAG_RACY      8  /* Algorithm 3 as printed: inside a colour class every spin decides on
+                                 the G it reads at that moment and adds its change with an atomic;
+                                 not deterministic, W ignored; grid-scale path (one instance) only */
 
 typedef struct gdi_ctx gdi_ctx;  /* opaque; owned by the library */
 

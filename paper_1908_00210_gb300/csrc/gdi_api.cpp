@@ -622,7 +622,8 @@ int gdi_anneal(gdi_ctx *c, const gdi_schedule *S, const gdi_run *run)
     R.max_row = max_row;
     R.key0 = key0;
     R.key1 = key1;
-    R.flags = (trace ? GDI_DEV_TRACE : 0) | ((run->flags & GDI_FLAG_NO_REPAIR) ? GDI_DEV_NO_REPAIR : 0);
+    R.flags = (trace ? GDI_DEV_TRACE : 0) | ((run->flags & GDI_FLAG_NO_REPAIR) ? GDI_DEV_NO_REPAIR : 0) |
+              ((run->flags & GDI_FLAG_RACY) ? GDI_DEV_RACY : 0);
     R.raw_G = c->raw_G.p;
     R.final_G = c->final_G.p;
     R.raw_cut = c->raw_cut.p;
@@ -641,7 +642,7 @@ int gdi_anneal(gdi_ctx *c, const gdi_schedule *S, const gdi_run *run)
     cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
     bool grid = false;
-    if (c->path == GDI_PATH_GRID) grid = true;
+    if (c->path == GDI_PATH_GRID || (run->flags & GDI_FLAG_RACY)) grid = true;
     else if (c->path == GDI_PATH_AUTO) grid = (c->Q == 1 && (c->max_n > 32768 || need > (size_t)max_optin));
     // kernel timing events (not while the stream is being captured into a graph)
     GdiKernelTimer timer{nullptr, 0, 0};

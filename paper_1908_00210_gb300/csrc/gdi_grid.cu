@@ -1359,6 +1359,83 @@ __global__ void __launch_bounds__(GB, 1) gdi_grid_sorted_kernel(GridArgs A)
     }
 }
 
+// Algorithm 3 as printed (GDI_FLAG_RACY): inside a colour class every spin decides at once on the
+// G it reads at that moment -- +1 flips iff G >= gamma, -1 iff G <= gamma', the same thresholds
+// (and Philox draws) as the serialised path -- and adds its change to G with an atomic, so a spin
+// sees the flips whose atomics landed before its read and not the others.  Not deterministic;
+// the windows play no part (W only sizes the blocks' shares).  One grid barrier per class.
+__global__ void __launch_bounds__(GB, 1) gdi_grid_racy_kernel(GridArgs A)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const GdiDevProblem &P = A.P;
+    const GdiDevRun &R = A.R;
+    const GdiGridScratch &X = A.X;
+    const int Pb = gridDim.x, p = blockIdx.x;
+    const int spc = A.spc;
+    const SortedLayout L = sorted_layout(spc, A.wpc, R.max_row, Pb);
+    int16_t *hb = reinterpret_cast<int16_t *>(smem_raw + L.off_h);
+    int32_t *gam = reinterpret_cast<int32_t *>(smem_raw + L.off_gam);
+    uint8_t *s0 = smem_raw + L.off_s0;
+    uint32_t *fm = reinterpret_cast<uint32_t *>(smem_raw + L.off_fm);
+    GSmem S = {};
+    S.longq = reinterpret_cast<int32_t *>(smem_raw + L.off_longq);
+    S.hist = reinterpret_cast<int32_t *>(smem_raw + L.off_hist);
+    S.nchunk = S.longq + spc;
+    S.row = reinterpret_cast<uint32_t *>(smem_raw + L.off_row);
+    S.misc = reinterpret_cast<int64_t *>(smem_raw + L.off_misc);
+    const int64_t base = P.node_off[0];
+    const int32_t n = (int32_t)(P.node_off[1] - base);
+    const int32_t *cls = P.class_ptr + P.class_off[0];
+    const int32_t ncls = P.class_off[1] - P.class_off[0] - 1;
+    const int nrep = A.nrep;
+
+    init_G(A, p, Pb, n, base);
+    if (!grid_sync(X)) return;
+    for (int sw = R.s_begin; sw < R.s_end; ++sw) {
+        const int32_t roff = R.tab_off[sw];
+        const int32_t rlen = R.tab_off[sw + 1] - roff;
+        for (int k = threadIdx.x; k < rlen; k += GB) S.row[k] = R.tab[roff + k];
+        const float Tsw = R.temp ? R.temp[sw] : 0.f;
+        __syncthreads();
+        for (int c = 0; c < ncls; ++c) {
+            int32_t a0, a1;
+            int nwin;
+            if (A.wbnd) {
+                const int32_t *bd = A.wbnd + (size_t)c * (Pb + 1);
+                a0 = min(cls[c] + bd[p] * P.W, cls[c + 1]);
+                a1 = min(cls[c] + bd[p + 1] * P.W, cls[c + 1]);
+            } else {
+                class_partition(cls[c], cls[c + 1], P.W, p, Pb, a0, a1, nwin);
+            }
+            const int32_t ns = a1 - a0;
+            range_thresholds(A, S, a0, a1, sw, true, 0, gam, 1, spc, s0, hb, rlen, Tsw);
+            for (int i = threadIdx.x; i < (ns + 3) / 4; i += GB) fm[i] = 0;
+            __syncthreads();
+            for (int r = 0; r < nrep; ++r) {
+                for (int32_t i = threadIdx.x; i < ns; i += GB) {
+                    const int32_t gm = gam[(size_t)r * spc + i];
+                    const bool neg = (s0[i] >> r) & 1;
+                    const int32_t g = *(volatile int32_t *)&X.Gcls[r];
+                    if (neg ? g <= gm : g >= gm) {
+                        atomicAdd(&X.Gcls[r], neg ? 2 : -2);
+                        atomicOr(&fm[i >> 2], 1u << (8 * (i & 3) + r));
+                    }
+                }
+            }
+            __syncthreads();
+            for (int32_t i = threadIdx.x; i < ns; i += GB) {
+                const uint32_t f = (fm[i >> 2] >> (8 * (i & 3))) & 0xFFu;
+                if (f) X.packed[base + a0 + i] = (uint8_t)(s0[i] ^ f);
+            }
+            if (!grid_sync(X)) return;
+        }
+        if (R.flags & GDI_DEV_TRACE) {
+            sweep_trace(A, p, Pb, n, base, sw);
+            if (!grid_sync(X)) return;
+        }
+    }
+}
+
 __global__ void set_word_kernel(unsigned int *p, unsigned int v) { *p = v; }
 
 // ---------------------------------------------------------------------------------------------
@@ -1627,8 +1704,11 @@ int gdi_launch_grid_anneal(const GdiDevProblem &P, const GdiDevRun &R, const Gdi
                            GdiKernelTimer *timer, void *stream)
 {
     cudaStream_t st = (cudaStream_t)stream;
-    const bool sorted = P.W <= SMAXW;
-    const void *kern = !sorted ? (const void *)gdi_grid_anneal_kernel
+    const bool racy = (R.flags & GDI_DEV_RACY) != 0;
+    const bool sorted = P.W <= SMAXW && !racy;
+    if (racy) smem = sorted_layout(spc, wpc, R.max_row, sms).total;
+    const void *kern = racy ? (const void *)gdi_grid_racy_kernel
+                     : !sorted ? (const void *)gdi_grid_anneal_kernel
                      : P.W <= 32 ? (const void *)gdi_grid_sorted_kernel<1>
                      : P.W <= 64 ? (const void *)gdi_grid_sorted_kernel<2>
                      : P.W <= 128 ? (const void *)gdi_grid_sorted_kernel<4>
@@ -1657,7 +1737,7 @@ int gdi_launch_grid_anneal(const GdiDevProblem &P, const GdiDevRun &R, const Gdi
         A.nrep = nrep;
         A.spc = spc;
         A.wpc = wpc;
-        A.wbnd = sorted ? wbnd : nullptr;
+        A.wbnd = (sorted || racy) ? wbnd : nullptr;
         void *args[] = {&A};
         const bool timed = timer && timer->ev && timer->n < timer->cap;
         if (timed) cudaEventRecord(timer->ev[2 * timer->n], st);

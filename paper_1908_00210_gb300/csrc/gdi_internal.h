@@ -105,6 +105,7 @@ int gdi_launch_gather_spins(const GdiDevProblem &P, const int8_t *spins_rank, in
 // flags mirrored from gdi.h
 #define GDI_DEV_TRACE 1
 #define GDI_DEV_NO_REPAIR 2
+#define GDI_DEV_RACY 4
 
 // device error codes written to GdiDevRun::err
 #define GDI_DEVERR_RANGE 1
