@@ -52,7 +52,10 @@ extern "C" {
 #define GDI_PAPER_PF   1   /* Alg. 2/3: argmin, then flip with probability P_f; P_f geometric pf0->pf1 */
 
 /* kernel paths (gdi_configure) */
-#define GDI_PATH_AUTO 0   /* CTA-resident unless a single instance has more than 32768 vertices  */
+#define GDI_PATH_AUTO 0   /* several instances: CTA-resident.  One instance (W >= 1): the path a
+                             cost model fitted on GB300 predicts faster: the grid-scale path for a
+                             few replicas of a graph above about 3,000 vertices, or whenever the
+                             CTA path's shared memory does not fit; CTA-resident otherwise      */
 #define GDI_PATH_CTA  1   /* one thread block anneals one (instance, replica), spins in shared memory */
 #define GDI_PATH_GRID 2   /* one instance over every SM (needs W >= 1); up to 8 replicas per pass;
                              W <= 256: sorted-window kernel, W > 256: tabulated-window kernel */

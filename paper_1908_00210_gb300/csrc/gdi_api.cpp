@@ -643,7 +643,23 @@ int gdi_anneal(gdi_ctx *c, const gdi_schedule *S, const gdi_run *run)
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
     bool grid = false;
     if (c->path == GDI_PATH_GRID || (run->flags & GDI_FLAG_RACY)) grid = true;
-    else if (c->path == GDI_PATH_AUTO) grid = (c->Q == 1 && (c->max_n > 32768 || need > (size_t)max_optin));
+    else if (c->path == GDI_PATH_AUTO && c->Q == 1 && c->W >= 1 && c->max_degree <= 32767) {
+        // one instance: the cheaper path by a cost model fitted on GB300 (BA and ER graphs of mean
+        // degree 10, 10^3 to 6.4*10^4 vertices, 1 to 608 replicas).  A CTA-resident sweep costs
+        // about 3.5 ns per (vertex + directed edge) per wave of resident blocks; a grid-scale sweep
+        // about 120 us (its per-class grid barriers) + 0.016 ns per (vertex + edge) per group of 8
+        // replicas.  The crossover for 8 replicas is near 3,000 vertices.
+        int per_sm = 0;
+        if (need > (size_t)max_optin || gdi_cta_blocks_per_sm(P, R, c->block, &per_sm) != 0 || per_sm < 1) {
+            grid = true;
+        } else {
+            const double work = (double)c->N + (double)c->nnz;
+            const int64_t slots = (int64_t)sms * per_sm;
+            const double cta_s = (double)((c->R + slots - 1) / slots) * 3.5e-9 * work;
+            const double grid_s = (double)((c->R + 7) / 8) * (120e-6 + 0.016e-9 * work);
+            grid = grid_s < cta_s;
+        }
+    }
     // kernel timing events (not while the stream is being captured into a graph)
     GdiKernelTimer timer{nullptr, 0, 0};
     c->kev_pairs = 0;
@@ -854,9 +870,32 @@ int gdi_autotune(gdi_ctx *c, const gdi_schedule *S, int32_t probe_sweeps, int32_
     if (e == cudaSuccess) e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
     if (e != cudaSuccess) return cuda_fail(e, "autotune setup");
+    gdi_run run{};
+    run.seed = 0x5eedULL;
+    run.last_sweep = probe_sweeps;
+    run.flags = GDI_FLAG_NO_REPAIR;
+    run.stream = st;
+    // a first probe (also the warm-up) shows which path the current settings take; a CTA block
+    // that does not fit leaves the choice to the block-size candidates
+    int rc = gdi_anneal(c, S, &run);
+    bool grid_path = false;
+    if (rc == GDI_OK) {
+        e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) rc = cuda_fail(e, "autotune probe");
+        grid_path = c->used_grid;
+    } else if (rc == GDI_ERR_TOO_LARGE) {
+        rc = GDI_OK;
+    }
+    if (rc != GDI_OK) {
+        cudaStreamSynchronize(st);
+        c->stream = nullptr;
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        cudaStreamDestroy(st);
+        return rc;
+    }
     // candidate launch configurations: (block, grid cap); the grid path ignores the block size
     std::vector<std::pair<int, int>> cand;
-    const bool grid_path = c->path == GDI_PATH_GRID || (c->path == GDI_PATH_AUTO && c->Q == 1 && c->max_n > 32768);
     if (grid_path) {
         for (int g : {sms, (sms * 3) / 4, sms / 2}) cand.push_back({c->block, g});
     } else {
@@ -865,12 +904,7 @@ int gdi_autotune(gdi_ctx *c, const gdi_schedule *S, int32_t probe_sweeps, int32_
     }
     const int keep_block = c->block, keep_grid = c->grid_limit;
     float best = 1e30f;
-    int best_b = keep_block, best_g = keep_grid, rc = GDI_OK;
-    gdi_run run{};
-    run.seed = 0x5eedULL;
-    run.last_sweep = probe_sweeps;
-    run.flags = GDI_FLAG_NO_REPAIR;
-    run.stream = st;
+    int best_b = keep_block, best_g = keep_grid;
     for (const auto &cg : cand) {
         c->block = cg.first;
         c->grid_limit = cg.second;

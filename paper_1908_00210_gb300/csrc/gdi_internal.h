@@ -79,6 +79,8 @@ int gdi_launch_init(const GdiDevProblem &P, int8_t *spins, const int8_t *init_or
 int gdi_launch_cta_anneal(const GdiDevProblem &P, const GdiDevRun &R, int block, int grid_limit,
                           void *stream, int *grid_used, size_t *smem_used);
 int gdi_cta_smem_bytes(const GdiDevProblem &P, const GdiDevRun &R, int block, size_t *bytes, int *hist);
+// resident CTA-path blocks per SM for this problem and block size (0 when the block does not fit)
+int gdi_cta_blocks_per_sm(const GdiDevProblem &P, const GdiDevRun &R, int block, int *per_sm);
 // Grid plan for `sms` blocks: spans of ranks (spc) and windows (wpc) per block and per class, and
 // the dynamic shared memory; -1 if the instance does not fit smem_limit.
 int gdi_grid_plan(const GdiDevProblem &P, int max_row, int sms, size_t smem_limit, int *spc, int *wpc,

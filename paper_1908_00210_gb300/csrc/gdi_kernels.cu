@@ -448,7 +448,30 @@ int launch_cta(const GdiDevProblem &P, const GdiDevRun &R, int grid_limit, cudaS
     return (int)cudaGetLastError();
 }
 
+template <int BS>
+int cta_occupancy(const GdiDevProblem &P, const GdiDevRun &R, int *per_sm)
+{
+    const size_t smem = cta_smem(P, R, BS, hist_bins(P));
+    cudaError_t e = cudaFuncSetAttribute(gdi_cta_anneal_kernel<BS>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, gdi_cta_anneal_kernel<BS>, BS, smem);
+    return (int)e;
+}
+
 }  // namespace
+
+int gdi_cta_blocks_per_sm(const GdiDevProblem &P, const GdiDevRun &R, int block, int *per_sm)
+{
+    *per_sm = 0;
+    switch (block) {
+    case 128: return cta_occupancy<128>(P, R, per_sm);
+    case 256: return cta_occupancy<256>(P, R, per_sm);
+    case 512: return cta_occupancy<512>(P, R, per_sm);
+    case 1024: return cta_occupancy<1024>(P, R, per_sm);
+    default: return (int)cudaErrorInvalidValue;
+    }
+}
 
 int gdi_cta_smem_bytes(const GdiDevProblem &P, const GdiDevRun &R, int block, size_t *bytes, int *hist)
 {

@@ -109,3 +109,33 @@ def test_kernel_time_counts_sweep_launches(gdi):
     assert n2 == 1 and ms2 > 0
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("n,replicas,want", [(1000, 8, "cta"), (20000, 8, "grid"), (20000, 608, "cta")])
+def test_auto_path_follows_cost_model(gdi, n, replicas, want):
+    """One instance: the automatic path is the CTA-resident one for small graphs or many replicas
+    (one block per replica fills the GPU) and the grid-scale one for a few replicas of a larger
+    graph (every SM on one replica group); results are bit-exact either way."""
+    g = barabasi_albert(n, 5, 90 + n)
+    sch = gdi.Schedule(sweeps=6, t0=12.0, t1=0.2)
+    a = gdi.Annealer(g, A=1, B=4, W=256, replicas=replicas)
+    a.anneal(sch, 5)
+    path = a.last_launch()["path"]
+    cut = a.results()["final_cut"][0]
+    a.close()
+    assert path == (gdi.GDI_PATH_GRID if want == "grid" else gdi.GDI_PATH_CTA)
+    if replicas <= 8:
+        ref = oracle.anneal(g, A=1, B=4, W=256, t0=12.0, t1=0.2, sweeps=6, seed=5, replicas=replicas)
+        assert np.array_equal(cut, ref.final_cut)
+
+
+def test_autotune_under_auto_path(gdi):
+    g = barabasi_albert(20000, 5, 73)
+    sch = gdi.Schedule(sweeps=20, t0=12.0, t1=0.2)
+    a = gdi.Annealer(g, A=1, B=4, W=256, replicas=8)
+    a.anneal(sch, 3, flags=gdi.GDI_FLAG_TRACE)
+    d0 = a.trace()[0].copy()
+    tuned = a.autotune(sch, probe_sweeps=4)
+    a.anneal(sch, 3, flags=gdi.GDI_FLAG_TRACE)
+    assert np.array_equal(a.trace()[0], d0) and tuned["ms"] > 0
+    a.close()
