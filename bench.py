@@ -350,8 +350,6 @@ def run_ours(args, wl, rank, world, local):
 
 
 
-# kernels of ours per gdi_anneal: CTA path = init + anneal; grid path = init + (pack + anneal +
-# unpack) per 8-replica group + raw cut + repair (hist, select, ties, mark, apply) + final cut
 def launches_per_anneal(path: int, replicas: int) -> int:
     """Kernels of one gdi_anneal: grid path = initial spins, then per group of 8 replicas pack,
     sweep kernel, raw cut, unpack, five repair kernels, pack and final cut; CTA path = initial

@@ -78,6 +78,7 @@ struct gdi_ctx {
     DevBuf<int16_t> g_tables;
     DevBuf<int32_t> g_gin, g_Gcls, g_err, g_status, g_rhist, g_rties, g_rparams;
     DevBuf<unsigned int> g_bar;
+    DevBuf<unsigned long long> g_hfield;
     bool used_grid = false;
     // cost-weighted split of every colour class over the grid path's blocks: window costs (one
     // instance, W >= 1), and the device copy of the bounds for the last block count and cap
@@ -172,6 +173,7 @@ struct gdi_ctx {
         X.rflags = g_rflags.p;
         X.rties = g_rties.p;
         X.rparams = g_rparams.p;
+        X.hfield = g_hfield.p;
         X.spin_limit = 1ll << 26;
         X.bar_start = 0;
         return X;
@@ -712,6 +714,7 @@ int gdi_anneal(gdi_ctx *c, const gdi_schedule *S, const gdi_run *run)
         if (e == cudaSuccess) e = c->g_rties.alloc((size_t)8 * 152 * 4);
         if (e == cudaSuccess) e = c->g_rparams.alloc(32);
         if (e == cudaSuccess) e = c->g_bar.alloc(2);
+        if (e == cudaSuccess && c->W <= 256) e = c->g_hfield.alloc((size_t)2 * c->N);
         if (e != cudaSuccess) return fail(GDI_ERR_OOM, "device allocation failed (grid scratch)");
         cudaMemsetAsync(c->g_err.p, 0, sizeof(int32_t), st);
         cudaMemsetAsync(c->g_status.p, 0, 16 * sizeof(int32_t), st);

@@ -93,6 +93,7 @@ struct GridArgs {
     int rep_base, nrep;
     int spc, wpc;
     const int32_t *wbnd;    // [classes][blocks + 1] first window of every block, or null (even split)
+    unsigned long long *hf; // maintained fields (X.hfield) when this kernel keeps them, else null
 };
 
 // ---------------------------------------------------------------------------------------------
@@ -219,6 +220,46 @@ __device__ __forceinline__ void chunk8_warp(const GdiDevProblem &P, int64_t base
 #pragma unroll
     for (int k = 0; k < 8; ++k)
         sb[k] = warp_sum((int32_t)((aP >> (8 * k)) & 0xFF) - (int32_t)((aN >> (8 * k)) & 0xFF));
+}
+
+// Maintained local fields.  The fields of rank rk for the 8 replicas of a group live in two 64-bit
+// words, H[2 rk + q] = sum_k h_{4q+k} 2^(16 k) mod 2^64.  Every |h| <= max degree < 2^15, so a word
+// decodes exactly, and a flip adds its field changes to every neighbour's words with 64-bit atomic
+// adds: the spins of a colour class change only at the class end, and the next class reads fields
+// that are exact for the spins after the flips.
+__device__ __forceinline__ unsigned long long field_word(const int16_t *h)
+{
+    unsigned long long w = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) w += (unsigned long long)(long long)h[k] << (16 * k);
+    return w;
+}
+
+// decode one field word into four fields, returned as two pairs of 16-bit lanes
+__device__ __forceinline__ uint2 field_unword(unsigned long long w)
+{
+    long long v = (long long)w;
+    uint32_t o[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int32_t x = (int16_t)(v & 0xFFFF);
+        o[k] = (uint32_t)x & 0xFFFFu;
+        v = (v - x) >> 16;
+    }
+    return make_uint2(o[0] | (o[1] << 16), o[2] | (o[3] << 16));
+}
+
+// the field changes that flipping replicas f (bit k) of a rank with group bits s (bit k set: -1
+// before the flip) makes at a neighbour joined by weight +1: -2 where +1 -> -1, +2 where -1 -> +1
+__device__ __forceinline__ void flip_words(uint32_t f, uint32_t s, unsigned long long &d0, unsigned long long &d1)
+{
+    d0 = d1 = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        if (!((f >> k) & 1u)) continue;
+        const unsigned long long d = ((s >> k) & 1u) ? 2ull : ~1ull;        // +2 or -2 mod 2^64
+        if (k < 4) d0 += d << (16 * k); else d1 += d << (16 * (k - 4));
+    }
 }
 
 // In-place cumulative counts of bins[0, nb) by one warp: forward (bins[x] = base + sum_{b <= x})
@@ -434,9 +475,16 @@ __device__ void range_thresholds(const GridArgs &A, const GSmem &S, int32_t a0, 
     __shared__ int nlong;
     if (threadIdx.x == 0) nlong = 0;
     __syncthreads();
+    const bool kept = all_reps && A.hf != nullptr;
     for (int32_t i = threadIdx.x; i < ns; i += GB) {
         const int32_t rk = a0 + i;
         s0_out[i] = __ldcg(packed + base + rk);
+        if (kept) {
+            const ulonglong2 v = __ldcg(reinterpret_cast<const ulonglong2 *>(A.hf) + base + rk);
+            const uint2 lo = field_unword(v.x), hi = field_unword(v.y);
+            *reinterpret_cast<uint4 *>(hbuf + (size_t)i * 8) = make_uint4(lo.x, lo.y, hi.x, hi.y);
+            continue;
+        }
         const int64_t e0 = P.row_ptr[base + rk], e1 = P.row_ptr[base + rk + 1];
         if (all_reps && e1 - e0 > LONG_ROW) {
             S.longq[atomicAdd(&nlong, 1)] = i;
@@ -597,6 +645,42 @@ __device__ __noinline__ void init_G(const GridArgs &A, int p, int Pb, int32_t n,
 }
 
 // digest and cut of every replica after sweep sw (grid-wide atomics), and G after the sweep
+// maintained fields of every rank from the packed spins at launch start
+__device__ __noinline__ void init_fields(const GridArgs &A, int p, int Pb, int32_t n, int64_t base)
+{
+    const GdiDevProblem &P = A.P;
+    unsigned long long *H = A.hf;
+    for (int32_t rk = p * GB + threadIdx.x; rk < n; rk += Pb * GB) {
+        const int64_t e0 = P.row_ptr[base + rk], e1 = P.row_ptr[base + rk + 1];
+        if (e1 - e0 > LONG_ROW) continue;
+        int16_t h[8];
+        field8_thread(P, base, e0, e1, A.X.packed, h, -1);
+        H[2 * (base + rk)] = field_word(h);
+        H[2 * (base + rk) + 1] = field_word(h + 4);
+    }
+    // rows longer than LONG_ROW: one warp per row, chunk by chunk
+    const int lane = threadIdx.x & 31;
+    for (int32_t rk = p * NWARP + warp_id(); rk < n; rk += Pb * NWARP) {
+        const int64_t e0 = P.row_ptr[base + rk], e1 = P.row_ptr[base + rk + 1];
+        if (e1 - e0 <= LONG_ROW) continue;
+        int32_t swt = 0, sbt[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        for (int64_t c0 = e0; c0 < e1; c0 += LCHUNK) {
+            int32_t swv, sb[8];
+            chunk8_warp(P, base, c0, min(e1, c0 + (int64_t)LCHUNK), A.X.packed, swv, sb);
+            swt += swv;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) sbt[k] += sb[k];
+        }
+        if (lane == 0) {
+            int16_t h[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) h[k] = (int16_t)(swt - 2 * sbt[k]);
+            H[2 * (base + rk)] = field_word(h);
+            H[2 * (base + rk) + 1] = field_word(h + 4);
+        }
+    }
+}
+
 __device__ __noinline__ void sweep_trace(const GridArgs &A, int p, int Pb, int32_t n, int64_t base, int sw)
 {
     const GdiDevProblem &P = A.P;
@@ -1145,7 +1229,9 @@ __global__ void __launch_bounds__(GB, 1) gdi_grid_sorted_kernel(GridArgs A)
     const int nrep = A.nrep;
 
     init_G(A, p, Pb, n, base);
+    if (A.hf) init_fields(A, p, Pb, n, base);
     if (!grid_sync(X)) return;
+    __shared__ int npush;
 
     uint32_t epoch = 0;
     for (int sw = R.s_begin; sw < R.s_end; ++sw) {
@@ -1183,6 +1269,7 @@ __global__ void __launch_bounds__(GB, 1) gdi_grid_sorted_kernel(GridArgs A)
             }
             for (int i = threadIdx.x; i < (ns + 3) / 4; i += GB) fm[i] = 0;
             for (int i = threadIdx.x; i < 8 * L.fw; i += GB) fbits[i] = 0;
+            if (threadIdx.x == 0) npush = 0;
             __syncthreads();
             // ---- block table per replica: lanes hold lattice points lane and lane + 32
             int t0 = lane, t1 = lane + 32;
@@ -1343,10 +1430,93 @@ __global__ void __launch_bounds__(GB, 1) gdi_grid_sorted_kernel(GridArgs A)
                 }
             }
             __syncthreads();
-            for (int32_t i = threadIdx.x; i < ns; i += GB) {
-                uint32_t f = (fm[i >> 2] >> (8 * (i & 3))) & 0xFFu;
-                for (int r = 0; r < nrep; ++r) f |= ((fbits[(size_t)r * L.fw + (i >> 5)] >> (i & 31)) & 1u) << r;
+            // ---- write the flips; with maintained fields, push their field changes to the
+            // neighbours: a warp takes 32 consecutive ranks and walks the concatenated rows of its
+            // flipping ones lane by lane (rows longer than LONG_ROW go to a block queue instead)
+            uint32_t *pq = reinterpret_cast<uint32_t *>(S.longq);
+            for (int32_t i0 = warp * 32; i0 < ns; i0 += GB) {
+                const int32_t i = i0 + lane;
+                uint32_t f = 0;
+                if (i < ns) {
+                    f = (fm[i >> 2] >> (8 * (i & 3))) & 0xFFu;
+                    for (int r = 0; r < nrep; ++r) f |= ((fbits[(size_t)r * L.fw + (i >> 5)] >> (i & 31)) & 1u) << r;
+                }
                 if (f) X.packed[base + a0 + i] = (uint8_t)(s0[i] ^ f);
+                if (!A.hf || !__any_sync(0xFFFFFFFFu, f != 0)) continue;
+                int64_t e0 = 0;
+                int32_t d = 0;
+                unsigned long long d0 = 0, d1 = 0;
+                if (f) {
+                    e0 = P.row_ptr[base + a0 + i];
+                    d = (int32_t)(P.row_ptr[base + a0 + i + 1] - e0);
+                    if (d > LONG_ROW) {
+                        pq[atomicAdd(&npush, 1)] = (uint32_t)i | (f << 24);
+                        d = 0;
+                    } else {
+                        flip_words(f, s0[i], d0, d1);
+                    }
+                }
+                int32_t incl = d;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int32_t t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+                    if (lane >= o) incl += t;
+                }
+                const int32_t excl = incl - d;
+                const int32_t tot = __shfl_sync(0xFFFFFFFFu, incl, 31);
+                for (int32_t k0 = 0; k0 < tot; k0 += 4 * 32) {
+                    uint32_t cc[4];
+                    unsigned long long w0[4], w1[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        // owner of entry k: the last lane whose rows start at or before k
+                        const int32_t k = k0 + 32 * u + lane;
+                        int src = 0;
+#pragma unroll
+                        for (int st = 16; st > 0; st >>= 1)
+                            if (__shfl_sync(0xFFFFFFFFu, excl, src + st) <= k) src += st;
+                        const int64_t oe = __shfl_sync(0xFFFFFFFFu, e0, src);
+                        const int32_t ox = __shfl_sync(0xFFFFFFFFu, excl, src);
+                        w0[u] = __shfl_sync(0xFFFFFFFFu, d0, src);
+                        w1[u] = __shfl_sync(0xFFFFFFFFu, d1, src);
+                        cc[u] = k < tot ? __ldg(P.col + oe + (k - ox)) : 0u;
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        if (k0 + 32 * u + lane >= tot) continue;
+                        unsigned long long *w = A.hf + 2 * (base + (int64_t)(cc[u] & 0x7FFFFFFFu));
+                        const bool neg = (cc[u] >> 31) != 0;
+                        if (w0[u]) atomicAdd(w, neg ? 0ull - w0[u] : w0[u]);
+                        if (w1[u]) atomicAdd(w + 1, neg ? 0ull - w1[u] : w1[u]);
+                    }
+                }
+            }
+            if (A.hf) {
+                __syncthreads();
+                const int nq = npush;
+                for (int t = warp; t < nq; t += NWARP) {
+                    const uint32_t q = pq[t];
+                    const int32_t i = (int32_t)(q & 0xFFFFFFu);
+                    unsigned long long d0, d1;
+                    flip_words(q >> 24, s0[i], d0, d1);
+                    const int64_t e0 = P.row_ptr[base + a0 + i], e1 = P.row_ptr[base + a0 + i + 1];
+                    for (int64_t eb = e0; eb < e1; eb += 4 * 32) {
+                        uint32_t cc[4];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const int64_t e = eb + 32 * u + lane;
+                            cc[u] = e < e1 ? __ldg(P.col + e) : 0u;
+                        }
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            if (eb + 32 * u + lane >= e1) continue;
+                            unsigned long long *w = A.hf + 2 * (base + (int64_t)(cc[u] & 0x7FFFFFFFu));
+                            const bool neg = (cc[u] >> 31) != 0;
+                            if (d0) atomicAdd(w, neg ? 0ull - d0 : d0);
+                            if (d1) atomicAdd(w + 1, neg ? 0ull - d1 : d1);
+                        }
+                    }
+                }
             }
             if (!grid_sync(X)) return;
         }
@@ -1437,6 +1607,7 @@ __global__ void __launch_bounds__(GB, 1) gdi_grid_racy_kernel(GridArgs A)
 }
 
 __global__ void set_word_kernel(unsigned int *p, unsigned int v) { *p = v; }
+
 
 // ---------------------------------------------------------------------------------------------
 // replica group <-> int8 spins in rank space
@@ -1738,6 +1909,7 @@ int gdi_launch_grid_anneal(const GdiDevProblem &P, const GdiDevRun &R, const Gdi
         A.spc = spc;
         A.wpc = wpc;
         A.wbnd = (sorted || racy) ? wbnd : nullptr;
+        A.hf = sorted ? X.hfield : nullptr;
         void *args[] = {&A};
         const bool timed = timer && timer->ev && timer->n < timer->cap;
         if (timed) cudaEventRecord(timer->ev[2 * timer->n], st);

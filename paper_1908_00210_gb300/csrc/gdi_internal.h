@@ -41,6 +41,8 @@ struct GdiGridScratch {
     uint8_t *rflags;                 // [N] repair flips (bit per replica)
     int32_t *rties;                  // [8][blocks] repair ties per block
     int32_t *rparams;                // [8][4] repair k, majority, kappa, ties to take
+    unsigned long long *hfield;      // [N][2] maintained local fields of the replica group (the
+                                     // sorted-window path), or null: fields gathered every class
     long long spin_limit;            // polls before a device wait gives up (error word set)
     unsigned int bar_start;          // initial barrier arrival count (0; test hook: blocks)
 };

@@ -135,6 +135,7 @@ extern "C" int gdi_anneal_static(int32_t n, const int64_t *row_ptr, const uint32
     X.rflags = nullptr;
     X.rties = nullptr;
     X.rparams = nullptr;
+    X.hfield = nullptr;
     X.spin_limit = 1ll << 26;
     X.bar_start = 0;
 
