@@ -38,6 +38,7 @@ namespace {
 
 constexpr int GB = 768;                 // threads per block
 constexpr int NWARP = GB / 32;
+static_assert(GB % 32 == 0, "whole warps; the threshold loop keeps one replica per thread");
 constexpr int RT = 64;                  // tables cover G in [c - RT, c + RT]
 constexpr int TW = 2 * RT + 1;
 static_assert(TW == GDI_GRID_TW, "table width mismatch");
@@ -542,10 +543,8 @@ __device__ void range_thresholds(const GridArgs &A, const GSmem &S, int32_t a0, 
         const int32_t q0 = a0 >> 2, q1 = (a1 - 1) >> 2;
         const int nr = all_reps ? A.nrep : 1;
         const int a_shift = (P.A > 0 && (P.A & (P.A - 1)) == 0) ? 2 + __ffs(P.A) - 1 : -1;   // log2(4A)
-        const int64_t tasks = (int64_t)(q1 - q0 + 1) * nr;
-        for (int64_t t = threadIdx.x; t < tasks; t += GB) {
-            const int32_t qd = q0 + (int32_t)(t / nr);
-            const int r = all_reps ? (int)(t % nr) : one;
+        // one Philox block per (quad of ranks, replica)
+        auto quad = [&](int32_t qd, int r) {
             const uint4 u4 = philox4x32_10(make_uint4((uint32_t)qd, (uint32_t)sw, 0u,
                                                       (uint32_t)(A.rep_base + r)),
                                            A.R.key0, A.R.key1);
@@ -560,6 +559,14 @@ __device__ void range_thresholds(const GridArgs &A, const GSmem &S, int32_t a0, 
                 gam_out[(size_t)i * gis + (size_t)(all_reps ? r : 0) * grs] =
                     a_shift >= 0 ? gamma_of_shift(sg, h, es, P.A, P.B, a_shift) : gamma_of(sg, h, es, P.A, P.B);
             }
+        };
+        const int32_t nq = q1 - q0 + 1;
+        if (nr == 8) {
+            // a thread keeps one replica (GB is a multiple of 8): no division in the task loop
+            const int r = threadIdx.x & 7;
+            for (int32_t qq = threadIdx.x >> 3; qq < nq; qq += GB / 8) quad(q0 + qq, r);
+        } else {
+            for (int32_t t = threadIdx.x; t < nq * nr; t += GB) quad(q0 + t / nr, all_reps ? t % nr : one);
         }
     }
     __syncthreads();
