@@ -466,7 +466,7 @@ __device__ inline void class_partition(int32_t lo, int32_t hi, int W, int p, int
 // long-row partial sums live there before the thresholds are written).
 __device__ void range_thresholds(const GridArgs &A, const GSmem &S, int32_t a0, int32_t a1, int sw,
                                  bool all_reps, int one, int32_t *gam_out, int gis, int grs, uint8_t *s0_out,
-                                 int16_t *hbuf, int32_t rlen, float Tsw)
+                                 int16_t *hbuf, int32_t rlen, float Tsw, bool quad_rows = false)
 {
     const GdiDevProblem &P = A.P;
     const int64_t base = P.node_off[0];
@@ -561,7 +561,31 @@ __device__ void range_thresholds(const GridArgs &A, const GSmem &S, int32_t a0, 
             }
         };
         const int32_t nq = q1 - q0 + 1;
-        if (nr == 8) {
+        if (nr == 8 && quad_rows) {
+            // rows of stride grs = 4 mod 32 whose element a0 - (a0 mod 4) is 16-byte aligned: the four
+            // thresholds of a quad go out in one 16-byte store (ranks outside [a0, a1) store 0)
+            const int r = threadIdx.x & 7;
+            int32_t *row = gam_out - (a0 & 3) + (size_t)r * grs;
+            for (int32_t qq = threadIdx.x >> 3; qq < nq; qq += GB / 8) {
+                const int32_t qd = q0 + qq;
+                const uint4 u4 = philox4x32_10(make_uint4((uint32_t)qd, (uint32_t)sw, 0u,
+                                                          (uint32_t)(A.rep_base + r)),
+                                               A.R.key0, A.R.key1);
+                int32_t g[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int32_t rk = 4 * qd + j;
+                    g[j] = 0;
+                    if (rk < a0 || rk >= a1) continue;
+                    const int32_t i = rk - a0;
+                    const int sg = ((s0_out[i] >> r) & 1) ? -1 : 1;
+                    const int32_t h = hbuf[(size_t)i * 8 + r];
+                    const int32_t es = estar_of(S.row, rlen, A.R.mode, word_of(u4, j), Tsw);
+                    g[j] = a_shift >= 0 ? gamma_of_shift(sg, h, es, P.A, P.B, a_shift) : gamma_of(sg, h, es, P.A, P.B);
+                }
+                *reinterpret_cast<int4 *>(row + 4 * qq) = make_int4(g[0], g[1], g[2], g[3]);
+            }
+        } else if (nr == 8) {
             // a thread keeps one replica (GB is a multiple of 8): no division in the task loop
             const int r = threadIdx.x & 7;
             for (int32_t qq = threadIdx.x >> 3; qq < nq; qq += GB / 8) quad(q0 + qq, r);
@@ -955,6 +979,7 @@ struct SortedLayout {
     size_t off_h, off_gam, off_s0, off_fm, off_fbits, off_longq, off_smap, off_hist, off_walk, off_row,
         off_misc, total;
     int fw;                             // words of one replica's flip bitmap
+    int gs;                             // threshold row stride (ints): >= spc + 7, 4 mod 32
 };
 
 __host__ __device__ inline SortedLayout sorted_layout(int spc, int wpc, int max_row, int P)
@@ -962,7 +987,10 @@ __host__ __device__ inline SortedLayout sorted_layout(int spc, int wpc, int max_
     SortedLayout L;
     size_t o = 0;
     L.off_h = o; o = align16(o + (size_t)spc * 8 * sizeof(int16_t));      // fields, then rel
-    L.off_gam = o; o = align16(o + (size_t)spc * 8 * sizeof(int32_t));    // thresholds [r][spc]
+    // thresholds [r][gs]: a row starts 4 words (16 banks' worth of bytes) after the previous
+    // one's bank, so the 8 replicas' 16-byte stores of one quad of ranks hit disjoint banks
+    L.gs = ((spc + 3 + 31) & ~31) + 4;
+    L.off_gam = o; o = align16(o + (size_t)L.gs * 8 * sizeof(int32_t));
     L.off_s0 = o; o = align16(o + (size_t)spc);
     L.off_fm = o; o = align16(o + (size_t)((spc + 3) / 4) * sizeof(uint32_t));
     L.fw = spc / 32 + 2;
@@ -1264,12 +1292,14 @@ __global__ void __launch_bounds__(GB, 1) gdi_grid_sorted_kernel(GridArgs A)
             const int32_t ns = a1 - a0;
             if (threadIdx.x < nrep) Gc[threadIdx.x] = *(volatile int32_t *)&X.Gcls[threadIdx.x];
             // ---- thresholds of my ranks (ends with a block barrier)
-            range_thresholds(A, S, a0, a1, sw, true, 0, gam, 1, spc, s0, hb, rlen, Tsw);
+            // thresholds of rank a0 + i for replica r at gamc[r * gs + i]
+            int32_t *gamc = gam + (a0 & 3);
+            range_thresholds(A, S, a0, a1, sw, true, 0, gamc, 1, L.gs, s0, hb, rlen, Tsw, true);
             // ---- sorted groups: rel values and stage maps of every (window, replica)
             for (int task = warp; task < nwin * nrep; task += NWARP) {
                 const int kk = task / nrep, r = task % nrep;
                 const int ws = kk * W, wlen = min(W, ns - ws);
-                const int32_t *gr = gam + (size_t)r * spc;
+                const int32_t *gr = gamc + (size_t)r * L.gs;
                 int16_t *rr = hb + (size_t)r * spc;
                 StageMap *o = smap + ((size_t)kk * 8 + r) * 2;
                 window_maps<SL>(gr, s0, rr, ws, wlen, r, Gc[r], o);
@@ -1370,7 +1400,7 @@ __global__ void __launch_bounds__(GB, 1) gdi_grid_sorted_kernel(GridArgs A)
                     const bool need_exact = idx < 0 || own < 0;
                     uint32_t *fb = fbits + (size_t)r * L.fw;
                     int32_t x = gin - c0;
-                    const int32_t *gr = gam + (size_t)r * spc;
+                    const int32_t *gr = gamc + (size_t)r * L.gs;
                     const int16_t *rr = hb + (size_t)r * spc;
                     int32_t *bins = hist + (size_t)warp * HA;
                     for (int kk = 0; kk < nwin; ++kk) {
