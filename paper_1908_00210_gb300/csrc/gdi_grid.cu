@@ -95,6 +95,7 @@ struct GridArgs {
     int spc, wpc;
     const int32_t *wbnd;    // [classes][blocks + 1] first window of every block, or null (even split)
     unsigned long long *hf; // maintained fields (X.hfield) when this kernel keeps them, else null
+    bool es_pre;            // sorted path: E* of the next class drawn ahead into shared memory
 };
 
 // ---------------------------------------------------------------------------------------------
@@ -459,6 +460,39 @@ __device__ inline void class_partition(int32_t lo, int32_t hi, int W, int p, int
     nwin = k1 - k0;
 }
 
+// E* in 16 bits: the sentinels at the ends of the range (values are 0..max_row < 32000 or -1)
+__device__ __forceinline__ int16_t es_encode(int32_t e)
+{
+    return e == ES_NONE ? (int16_t)INT16_MIN : (e == ES_ALL ? (int16_t)INT16_MAX : (int16_t)e);
+}
+__device__ __forceinline__ int32_t es_decode(int16_t v)
+{
+    return v == INT16_MIN ? ES_NONE : (v == INT16_MAX ? ES_ALL : (int32_t)v);
+}
+
+// E*(u) of every (rank, replica) of [a0, a1) into rows es_out[r * es_s + 4 qq + j] for rank
+// 4 (q0 + qq) + j (q0 = a0 / 4), by the threads t0 .. t0 + nth - 1 (nth a multiple of 8).  The draws
+// depend on (rank, sweep, replica) and the table row only, so they can be made before the spins of
+// the range are known.
+__device__ void estar_ahead(const GridArgs &A, const GSmem &S, int32_t a0, int32_t a1, int sw, int16_t *es_out,
+                            int es_s, int32_t rlen, float Tsw, int t, int nth)
+{
+    if (a1 <= a0) return;
+    const int32_t q0 = a0 >> 2, q1 = (a1 - 1) >> 2, nq = q1 - q0 + 1;
+    const int r = t & 7;
+    if (r >= A.nrep) return;
+    for (int32_t qq = t >> 3; qq < nq; qq += nth >> 3) {
+        const int32_t qd = q0 + qq;
+        const uint4 u4 = philox4x32_10(make_uint4((uint32_t)qd, (uint32_t)sw, 0u, (uint32_t)(A.rep_base + r)),
+                                       A.R.key0, A.R.key1);
+        uint32_t e[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            e[j] = (uint16_t)es_encode(estar_of(S.row, rlen, A.R.mode, word_of(u4, j), Tsw));
+        *reinterpret_cast<uint2 *>(es_out + (size_t)r * es_s + 4 * qq) = make_uint2(e[0] | (e[1] << 16), e[2] | (e[3] << 16));
+    }
+}
+
 // Thresholds of the spin range [a0, a1).  all_reps: every replica, threshold of (i, r) stored at
 // gam_out[i * gis + r * grs] (fields in hbuf [i*8 + r], rows longer than LONG_ROW summed by a
 // warp).  Otherwise only replica `one`, stored at gam_out[i * gis] with fields [i] (thread-serial
@@ -466,7 +500,8 @@ __device__ inline void class_partition(int32_t lo, int32_t hi, int W, int p, int
 // long-row partial sums live there before the thresholds are written).
 __device__ void range_thresholds(const GridArgs &A, const GSmem &S, int32_t a0, int32_t a1, int sw,
                                  bool all_reps, int one, int32_t *gam_out, int gis, int grs, uint8_t *s0_out,
-                                 int16_t *hbuf, int32_t rlen, float Tsw, bool quad_rows = false)
+                                 int16_t *hbuf, int32_t rlen, float Tsw, bool quad_rows = false,
+                                 const int16_t *es_in = nullptr, int es_s = 0)
 {
     const GdiDevProblem &P = A.P;
     const int64_t base = P.node_off[0];
@@ -568,9 +603,21 @@ __device__ void range_thresholds(const GridArgs &A, const GSmem &S, int32_t a0, 
             int32_t *row = gam_out - (a0 & 3) + (size_t)r * grs;
             for (int32_t qq = threadIdx.x >> 3; qq < nq; qq += GB / 8) {
                 const int32_t qd = q0 + qq;
-                const uint4 u4 = philox4x32_10(make_uint4((uint32_t)qd, (uint32_t)sw, 0u,
-                                                          (uint32_t)(A.rep_base + r)),
-                                               A.R.key0, A.R.key1);
+                int32_t ev[4];
+                if (es_in) {
+                    // E* drawn ahead (same rows layout: quad qq at 4 qq)
+                    const uint2 w = *reinterpret_cast<const uint2 *>(es_in + (size_t)r * es_s + 4 * qq);
+                    ev[0] = es_decode((int16_t)(w.x & 0xFFFFu));
+                    ev[1] = es_decode((int16_t)(w.x >> 16));
+                    ev[2] = es_decode((int16_t)(w.y & 0xFFFFu));
+                    ev[3] = es_decode((int16_t)(w.y >> 16));
+                } else {
+                    const uint4 u4 = philox4x32_10(make_uint4((uint32_t)qd, (uint32_t)sw, 0u,
+                                                              (uint32_t)(A.rep_base + r)),
+                                                   A.R.key0, A.R.key1);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) ev[j] = estar_of(S.row, rlen, A.R.mode, word_of(u4, j), Tsw);
+                }
                 int32_t g[4];
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
@@ -580,7 +627,7 @@ __device__ void range_thresholds(const GridArgs &A, const GSmem &S, int32_t a0, 
                     const int32_t i = rk - a0;
                     const int sg = ((s0_out[i] >> r) & 1) ? -1 : 1;
                     const int32_t h = hbuf[(size_t)i * 8 + r];
-                    const int32_t es = estar_of(S.row, rlen, A.R.mode, word_of(u4, j), Tsw);
+                    const int32_t es = ev[j];
                     g[j] = a_shift >= 0 ? gamma_of_shift(sg, h, es, P.A, P.B, a_shift) : gamma_of(sg, h, es, P.A, P.B);
                 }
                 *reinterpret_cast<int4 *>(row + 4 * qq) = make_int4(g[0], g[1], g[2], g[3]);
@@ -976,13 +1023,14 @@ struct StageMap {
 };
 
 struct SortedLayout {
-    size_t off_h, off_gam, off_s0, off_fm, off_fbits, off_longq, off_smap, off_hist, off_walk, off_row,
+    size_t off_h, off_gam, off_es, off_s0, off_fm, off_fbits, off_longq, off_smap, off_hist, off_walk, off_row,
         off_misc, total;
     int fw;                             // words of one replica's flip bitmap
     int gs;                             // threshold row stride (ints): >= spc + 7, 4 mod 32
+    int es;                             // E* row stride (int16): >= spc + 7, 16 mod 32; 0 = no E* rows
 };
 
-__host__ __device__ inline SortedLayout sorted_layout(int spc, int wpc, int max_row, int P)
+__host__ __device__ inline SortedLayout sorted_layout(int spc, int wpc, int max_row, int P, bool es_rows)
 {
     SortedLayout L;
     size_t o = 0;
@@ -991,6 +1039,9 @@ __host__ __device__ inline SortedLayout sorted_layout(int spc, int wpc, int max_
     // one's bank, so the 8 replicas' 16-byte stores of one quad of ranks hit disjoint banks
     L.gs = ((spc + 3 + 31) & ~31) + 4;
     L.off_gam = o; o = align16(o + (size_t)L.gs * 8 * sizeof(int32_t));
+    // E* of the next class's ranks [r][es], drawn ahead by the warps that do not walk
+    L.es = es_rows ? ((spc + 3 + 31) & ~31) + 16 : 0;
+    L.off_es = o; o = align16(o + (size_t)L.es * 8 * sizeof(int16_t));
     L.off_s0 = o; o = align16(o + (size_t)spc);
     L.off_fm = o; o = align16(o + (size_t)((spc + 3) / 4) * sizeof(uint32_t));
     L.fw = spc / 32 + 2;
@@ -1231,9 +1282,10 @@ __global__ void __launch_bounds__(GB, 1) gdi_grid_sorted_kernel(GridArgs A)
     const int Pb = gridDim.x, p = blockIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int spc = A.spc;
-    const SortedLayout L = sorted_layout(spc, A.wpc, R.max_row, Pb);
+    const SortedLayout L = sorted_layout(spc, A.wpc, R.max_row, Pb, A.es_pre);
     int16_t *hb = reinterpret_cast<int16_t *>(smem_raw + L.off_h);   // fields [i*8 + r], then rel [r*spc + i]
     int32_t *gam = reinterpret_cast<int32_t *>(smem_raw + L.off_gam);
+    int16_t *esb = reinterpret_cast<int16_t *>(smem_raw + L.off_es);   // E* drawn ahead [r][L.es]
     uint8_t *s0 = smem_raw + L.off_s0;
     uint32_t *fm = reinterpret_cast<uint32_t *>(smem_raw + L.off_fm);
     StageMap *smap = reinterpret_cast<StageMap *>(smem_raw + L.off_smap);
@@ -1268,6 +1320,18 @@ __global__ void __launch_bounds__(GB, 1) gdi_grid_sorted_kernel(GridArgs A)
     if (!grid_sync(X)) return;
     __shared__ int npush;
 
+    // my ranks [x0, x1) of class cc
+    auto class_range = [&](int cc, int32_t &x0, int32_t &x1, int &nw) {
+        const int32_t lo = cls[cc], hi = cls[cc + 1];
+        if (A.wbnd) {
+            const int32_t *bd = A.wbnd + (size_t)cc * (Pb + 1);
+            x0 = min(lo + bd[p] * W, hi);
+            x1 = min(lo + bd[p + 1] * W, hi);
+            nw = bd[p + 1] - bd[p];
+        } else {
+            class_partition(lo, hi, W, p, Pb, x0, x1, nw);
+        }
+    };
     uint32_t epoch = 0;
     for (int sw = R.s_begin; sw < R.s_end; ++sw) {
         const int32_t roff = R.tab_off[sw];
@@ -1276,25 +1340,19 @@ __global__ void __launch_bounds__(GB, 1) gdi_grid_sorted_kernel(GridArgs A)
         const float Tsw = R.temp ? R.temp[sw] : 0.f;
         const bool plus_first = (sw & 1) == 0;
         __syncthreads();
+        bool have_es = false;                  // esb holds E* of this class's ranks
         for (int c = 0; c < ncls; ++c) {
             ++epoch;
-            const int32_t lo = cls[c], hi = cls[c + 1];
             int32_t a0, a1;
             int nwin;
-            if (A.wbnd) {
-                const int32_t *bd = A.wbnd + (size_t)c * (Pb + 1);
-                a0 = min(lo + bd[p] * W, hi);
-                a1 = min(lo + bd[p + 1] * W, hi);
-                nwin = bd[p + 1] - bd[p];
-            } else {
-                class_partition(lo, hi, W, p, Pb, a0, a1, nwin);
-            }
+            class_range(c, a0, a1, nwin);
             const int32_t ns = a1 - a0;
             if (threadIdx.x < nrep) Gc[threadIdx.x] = *(volatile int32_t *)&X.Gcls[threadIdx.x];
             // ---- thresholds of my ranks (ends with a block barrier)
             // thresholds of rank a0 + i for replica r at gamc[r * gs + i]
             int32_t *gamc = gam + (a0 & 3);
-            range_thresholds(A, S, a0, a1, sw, true, 0, gamc, 1, L.gs, s0, hb, rlen, Tsw, true);
+            range_thresholds(A, S, a0, a1, sw, true, 0, gamc, 1, L.gs, s0, hb, rlen, Tsw, true,
+                             have_es ? esb : nullptr, L.es);
             // ---- sorted groups: rel values and stage maps of every (window, replica)
             for (int task = warp; task < nwin * nrep; task += NWARP) {
                 const int kk = task / nrep, r = task % nrep;
@@ -1465,7 +1523,14 @@ __global__ void __launch_bounds__(GB, 1) gdi_grid_sorted_kernel(GridArgs A)
                         if (p == Pb - 1) X.Gcls[r] = gout;
                     }
                 }
+            } else if (A.es_pre && c + 1 < ncls) {
+                // the warps that do not walk draw the next class's E* meanwhile
+                int32_t b0, b1;
+                int nwb;
+                class_range(c + 1, b0, b1, nwb);
+                estar_ahead(A, S, b0, b1, sw, esb, L.es, rlen, Tsw, threadIdx.x - nrep * 32, GB - nrep * 32);
             }
+            have_es = A.es_pre && c + 1 < ncls;
             __syncthreads();
             // ---- write the flips; with maintained fields, push their field changes to the
             // neighbours: a warp takes 32 consecutive ranks and walks the concatenated rows of its
@@ -1579,7 +1644,7 @@ __global__ void __launch_bounds__(GB, 1) gdi_grid_racy_kernel(GridArgs A)
     const GdiGridScratch &X = A.X;
     const int Pb = gridDim.x, p = blockIdx.x;
     const int spc = A.spc;
-    const SortedLayout L = sorted_layout(spc, A.wpc, R.max_row, Pb);
+    const SortedLayout L = sorted_layout(spc, A.wpc, R.max_row, Pb, A.es_pre);
     int16_t *hb = reinterpret_cast<int16_t *>(smem_raw + L.off_h);
     int32_t *gam = reinterpret_cast<int32_t *>(smem_raw + L.off_gam);
     uint8_t *s0 = smem_raw + L.off_s0;
@@ -1859,7 +1924,10 @@ int gdi_grid_plan(const GdiDevProblem &P, int max_row, int sms, size_t smem_limi
     if (P.W <= SMAXW) {
         // the cost-weighted split stays within the even share of windows per block: more shared
         // memory per block (less L1) costs more than the finer balance gains
-        *smem = sorted_layout(*spc, *wpc, max_row, sms).total;
+        // with rows for the E* drawn ahead when they fit, else without
+        *smem = sorted_layout(*spc, *wpc, max_row, sms, true).total;
+        if (*smem <= smem_limit) return 0;
+        *smem = sorted_layout(*spc, *wpc, max_row, sms, false).total;
         return *smem <= smem_limit ? 0 : -1;
     }
     // the tabulated path keeps the long rows' chunk counts in the histogram area, and its exact
@@ -1914,7 +1982,7 @@ int gdi_launch_grid_anneal(const GdiDevProblem &P, const GdiDevRun &R, const Gdi
     cudaStream_t st = (cudaStream_t)stream;
     const bool racy = (R.flags & GDI_DEV_RACY) != 0;
     const bool sorted = P.W <= SMAXW && !racy;
-    if (racy) smem = sorted_layout(spc, wpc, R.max_row, sms).total;
+    if (racy) smem = sorted_layout(spc, wpc, R.max_row, sms, false).total;
     const void *kern = racy ? (const void *)gdi_grid_racy_kernel
                      : !sorted ? (const void *)gdi_grid_anneal_kernel
                      : P.W <= 32 ? (const void *)gdi_grid_sorted_kernel<1>
@@ -1947,6 +2015,7 @@ int gdi_launch_grid_anneal(const GdiDevProblem &P, const GdiDevRun &R, const Gdi
         A.wpc = wpc;
         A.wbnd = (sorted || racy) ? wbnd : nullptr;
         A.hf = sorted ? X.hfield : nullptr;
+        A.es_pre = sorted && R.max_row < 32000 && smem >= sorted_layout(spc, wpc, R.max_row, sms, true).total;
         void *args[] = {&A};
         const bool timed = timer && timer->ev && timer->n < timer->cap;
         if (timed) cudaEventRecord(timer->ev[2 * timer->n], st);
