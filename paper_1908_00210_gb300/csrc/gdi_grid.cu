@@ -470,11 +470,12 @@ __device__ __forceinline__ int32_t es_decode(int16_t v)
     return v == INT16_MIN ? ES_NONE : (v == INT16_MAX ? ES_ALL : (int32_t)v);
 }
 
-// E*(u) of every (rank, replica) of [a0, a1) into rows es_out[r * es_s + 4 qq + j] for rank
-// 4 (q0 + qq) + j (q0 = a0 / 4), by the threads t0 .. t0 + nth - 1 (nth a multiple of 8).  The draws
+// E*(u) of every (rank, replica) of [a0, a1) at sweep sw (table row `row` of length rlen) into rows
+// es_out[r * es_s + 4 qq + j] for rank 4 (q0 + qq) + j (q0 = a0 / 4), by the threads t of 0 .. nth - 1
+// (nth a multiple of 8).  The draws
 // depend on (rank, sweep, replica) and the table row only, so they can be made before the spins of
 // the range are known.
-__device__ void estar_ahead(const GridArgs &A, const GSmem &S, int32_t a0, int32_t a1, int sw, int16_t *es_out,
+__device__ void estar_ahead(const GridArgs &A, const uint32_t *row, int32_t a0, int32_t a1, int sw, int16_t *es_out,
                             int es_s, int32_t rlen, float Tsw, int t, int nth)
 {
     if (a1 <= a0) return;
@@ -488,7 +489,7 @@ __device__ void estar_ahead(const GridArgs &A, const GSmem &S, int32_t a0, int32
         uint32_t e[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j)
-            e[j] = (uint16_t)es_encode(estar_of(S.row, rlen, A.R.mode, word_of(u4, j), Tsw));
+            e[j] = (uint16_t)es_encode(estar_of(row, rlen, A.R.mode, word_of(u4, j), Tsw));
         *reinterpret_cast<uint2 *>(es_out + (size_t)r * es_s + 4 * qq) = make_uint2(e[0] | (e[1] << 16), e[2] | (e[3] << 16));
     }
 }
@@ -1333,6 +1334,7 @@ __global__ void __launch_bounds__(GB, 1) gdi_grid_sorted_kernel(GridArgs A)
         }
     };
     uint32_t epoch = 0;
+    bool have_es = false;                      // esb holds E* of the current class's ranks
     for (int sw = R.s_begin; sw < R.s_end; ++sw) {
         const int32_t roff = R.tab_off[sw];
         const int32_t rlen = R.tab_off[sw + 1] - roff;
@@ -1340,7 +1342,6 @@ __global__ void __launch_bounds__(GB, 1) gdi_grid_sorted_kernel(GridArgs A)
         const float Tsw = R.temp ? R.temp[sw] : 0.f;
         const bool plus_first = (sw & 1) == 0;
         __syncthreads();
-        bool have_es = false;                  // esb holds E* of this class's ranks
         for (int c = 0; c < ncls; ++c) {
             ++epoch;
             int32_t a0, a1;
@@ -1523,14 +1524,20 @@ __global__ void __launch_bounds__(GB, 1) gdi_grid_sorted_kernel(GridArgs A)
                         if (p == Pb - 1) X.Gcls[r] = gout;
                     }
                 }
-            } else if (A.es_pre && c + 1 < ncls) {
-                // the warps that do not walk draw the next class's E* meanwhile
+            } else if (A.es_pre && (c + 1 < ncls || sw + 1 < R.s_end)) {
+                // the warps that do not walk draw the next class's E* meanwhile (after the last
+                // class: the next sweep's first class, from that sweep's table row)
+                const bool same = c + 1 < ncls;
+                const int sn = same ? sw : sw + 1;
                 int32_t b0, b1;
                 int nwb;
-                class_range(c + 1, b0, b1, nwb);
-                estar_ahead(A, S, b0, b1, sw, esb, L.es, rlen, Tsw, threadIdx.x - nrep * 32, GB - nrep * 32);
+                class_range(same ? c + 1 : 0, b0, b1, nwb);
+                const int32_t ro = R.tab_off[sn];
+                estar_ahead(A, same ? S.row : R.tab + ro, b0, b1, sn, esb, L.es,
+                            same ? rlen : R.tab_off[sn + 1] - ro, same ? Tsw : (R.temp ? R.temp[sn] : 0.f),
+                            threadIdx.x - nrep * 32, GB - nrep * 32);
             }
-            have_es = A.es_pre && c + 1 < ncls;
+            have_es = A.es_pre && (c + 1 < ncls || sw + 1 < R.s_end);
             __syncthreads();
             // ---- write the flips; with maintained fields, push their field changes to the
             // neighbours: a warp takes 32 consecutive ranks and walks the concatenated rows of its
