@@ -530,7 +530,7 @@ __device__ void range_thresholds(const GridArgs &A, const GSmem &S, int32_t a0, 
         }
     }
     __syncthreads();
-    if (all_reps) {
+    if (all_reps && !kept) {
         // long rows: chunks of LCHUNK entries are warp tasks; partial sums meet in shared memory.
         // acc[i*8 + k] = sum_j w_ij bit_k(j) lives in the threshold array (free until the
         // thresholds are written below); sum_j w_ij lives in the first 4 bytes of the row's
@@ -1946,6 +1946,8 @@ int gdi_grid_plan(const GdiDevProblem &P, int max_row, int sms, size_t smem_limi
     return *smem <= smem_limit ? 0 : -1;
 }
 
+constexpr double LAST_SHARE = 0.6;
+
 void gdi_grid_window_bounds(const int64_t *cost, const int64_t *cost_off, int num_classes, int blocks,
                             int wpc, int32_t *bnd)
 {
@@ -1955,12 +1957,14 @@ void gdi_grid_window_bounds(const int64_t *cost, const int64_t *cost_off, int nu
         int32_t *K = bnd + (size_t)c * (blocks + 1);
         int64_t total = 0;
         for (int k = 0; k < nw; ++k) total += w[k];
-        // ideal cut before block p: the window boundary nearest to p/blocks of the class's cost
+        // ideal cut before block p: the window boundary nearest to p shares of the class's cost,
+        // where the last block takes LAST_SHARE of a share: it walks last, so its replay and push
+        // end the class
         int k = 0;
         int64_t pre = 0;
         K[0] = 0;
         for (int p = 1; p < blocks; ++p) {
-            const double target = (double)total * p / blocks;
+            const double target = (double)total * p / (blocks - 1 + LAST_SHARE);
             while (k < nw && (double)(pre + w[k]) <= target) pre += w[k++];
             int cut = k;
             if (k < nw && (double)(pre + w[k]) - target < target - (double)pre) cut = k + 1;
