@@ -999,11 +999,11 @@ __global__ void __launch_bounds__(GB, 1) gdi_grid_anneal_kernel(GridArgs A)
 // Block maps: on the lattice x = G - c in {-64, -62, ..., 62} (64 points; G - c is always even) a
 // group is a staircase: index j -> ylo + popcount(mask & bits below j), read from where the a_k
 // (b_k) fall.  The maps of a block's windows are composed per replica into a 64-entry byte table
-// (two lattice points per lane; -1 = leaves the lattice) and published with a release flag.  The
-// last block of every run of 16 blocks also composes the run's tables into a run table.  Every
-// block then fetches the run tables before it and the block tables of its own run (flag polls,
-// one fence, all fetches at once) and looks its exact entering G up from c: at most
-// 160 / 16 + 15 byte lookups, without a grid barrier.  Where the walk leaves the lattice, the block whose table failed publishes its exact
+// (two lattice points per lane; -1 = leaves the lattice) and published byte by byte with the class
+// parity in every byte, so a reader needs no flag.  The last block of every run of 16 blocks also
+// composes the run's tables into a run table.  Every block then fetches the run tables before it
+// and the block tables of its own run (one poll of all of them per round trip) and looks its exact
+// entering G up from c: at most 160 / 16 + 15 byte lookups, without a grid barrier.  Where the walk leaves the lattice, the block whose table failed publishes its exact
 // outgoing G (it knows its own entering G and replays exactly), and the walk continues from it.
 // One grid barrier per class remains: the next class reads this class's spins.
 constexpr int SMAXW = 256;
@@ -1058,7 +1058,7 @@ __host__ __device__ inline SortedLayout sorted_layout(int spc, int wpc, int max_
 }
 
 // chain buffers carved from the scratch table area: exact outgoing G [P][8] (epoch << 32 | G),
-// block-table flags [P], run-table flags [NR], block tables [P][8][64], run tables [NR][8][64]
+// two unused flag areas [P] and [NR], block tables [P][8][64], run tables [NR][8][64]
 __host__ __device__ inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 __host__ __device__ inline size_t chain_off_flag(int P) { return align256((size_t)P * 8 * sizeof(uint64_t)); }
 __host__ __device__ inline size_t chain_off_rflag(int P) { return chain_off_flag(P) + align256((size_t)P * sizeof(uint32_t)); }
@@ -1071,16 +1071,6 @@ __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long
     unsigned long long v;
     asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
-}
-__device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t *p)
-{
-    uint32_t v;
-    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ void st_release_u32(uint32_t *p, uint32_t v)
-{
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 __device__ __forceinline__ void st_release_u64(unsigned long long *p, unsigned long long v)
 {
@@ -1228,38 +1218,85 @@ __device__ __forceinline__ int stage_apply(const StageMap &m, int t)
     return (y >= 0 && y < NT) ? y : -1;
 }
 
-// warp: fetch the byte tables of `cnt` entries (src + k * stride, k < cnt <= 32) into dst[k][64]
-__device__ __forceinline__ void fetch_tables(const int8_t *src, size_t stride, int cnt, int8_t *dst)
+// Published tables carry the class parity in bit 7 of every byte and the entry (-1 .. 63, -1 as
+// 0x7F) in the low 7 bits.  A byte is atomic on its own, so a reader that sees the parity of the
+// current class in all 64 bytes has the whole table: no flag, and one round trip per poll.  The
+// bytes of the previous class hold the other parity, and the chain area is zeroed at launch
+// (parity 0) while the first class has parity 1.
+__device__ __forceinline__ void st_tab_byte(int8_t *p, int v, uint32_t par)
 {
-    const int lane = threadIdx.x & 31;
-    if (lane < cnt) {
-        const uint4 *s4 = reinterpret_cast<const uint4 *>(src + (size_t)lane * stride);
-        const uint4 v0 = __ldcg(s4), v1 = __ldcg(s4 + 1), v2 = __ldcg(s4 + 2), v3 = __ldcg(s4 + 3);
-        uint4 *d4 = reinterpret_cast<uint4 *>(dst + (size_t)lane * NT);
-        d4[0] = v0;
-        d4[1] = v1;
-        d4[2] = v2;
-        d4[3] = v3;
-    }
-    __syncwarp();
+    const uint32_t b = ((uint32_t)v & 0x7Fu) | par;
+    asm volatile("st.relaxed.gpu.global.u8 [%0], %1;" ::"l"(p), "r"(b) : "memory");
 }
 
-// warp: bounded poll until every flag f[k * 1], k < cnt <= 32, holds `want` (relaxed loads, then one
-// fence).  Returns false (error word set) on timeout or when another block failed.
-__device__ __forceinline__ bool poll_flags(const uint32_t *f, int cnt, uint32_t want, const GdiGridScratch &X)
+__device__ __forceinline__ uint4 ld_tab16(const int8_t *p)
+{
+    uint4 v;
+    // no memory clobber: the four loads of a table may be in flight together; volatile keeps
+    // every poll's loads
+    asm volatile("ld.relaxed.gpu.global.v4.u32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(p));
+    return v;
+}
+
+// four table bytes: the low 7 bits, 0x7F mapped to 0xFF (-1)
+__device__ __forceinline__ uint32_t tab_decode(uint32_t w)
+{
+    const uint32_t v = w & 0x7F7F7F7Fu;
+    return v | ((v + 0x01010101u) & 0x80808080u);
+}
+
+// warp: copies the tables a + k * stride (k < na) to da + k * NT and b + k * stride (k < nb) to
+// db + k * NT, decoded, once every byte of them carries the parity `par` (lane k < na + nb <= 32
+// reads one table per poll).  Bounded wait; false on timeout or when another block failed.
+__device__ bool fetch_valid(const int8_t *a, int na, int8_t *da, const int8_t *b, int nb, int8_t *db,
+                            size_t stride, uint32_t par, const GdiGridScratch &X)
 {
     const int lane = threadIdx.x & 31;
-    bool ok = true;
-    if (lane < cnt) {
-        long long spins = 0;
-        while (ld_relaxed_u32(f + lane) != want) {
-            if (++spins > X.spin_limit) { atomicExch(X.err, GDI_DEVERR_TIMEOUT); ok = false; break; }
-            if ((spins & 63) == 0 && *(volatile int *)X.err) { ok = false; break; }
-            __nanosleep(20);
-        }
+    const int8_t *src = nullptr;
+    int8_t *dst = nullptr;
+    if (lane < na) {
+        src = a + (size_t)lane * stride;
+        dst = da + (size_t)lane * NT;
+    } else if (lane < na + nb) {
+        src = b + (size_t)(lane - na) * stride;
+        dst = db + (size_t)(lane - na) * NT;
     }
-    __threadfence();
-    return __all_sync(0xFFFFFFFFu, ok);
+    const uint32_t want = par ? 0x80808080u : 0u;
+    long long spins = 0;
+    bool ok = true;
+    for (;;) {
+        // every poll copies the decoded bytes; the last poll, where all are current, stays
+        bool good = true;
+        if (src) {
+            const uint4 v0 = ld_tab16(src), v1 = ld_tab16(src + 16), v2 = ld_tab16(src + 32),
+                        v3 = ld_tab16(src + 48);
+            const uint32_t m = (v0.x & v0.y & v0.z & v0.w & v1.x & v1.y & v1.z & v1.w & v2.x & v2.y & v2.z &
+                                v2.w & v3.x & v3.y & v3.z & v3.w) & 0x80808080u;
+            const uint32_t o = (v0.x | v0.y | v0.z | v0.w | v1.x | v1.y | v1.z | v1.w | v2.x | v2.y | v2.z |
+                                v2.w | v3.x | v3.y | v3.z | v3.w) & 0x80808080u;
+            good = par ? m == want : o == want;
+            uint4 *d4 = reinterpret_cast<uint4 *>(dst);
+            d4[0] = make_uint4(tab_decode(v0.x), tab_decode(v0.y), tab_decode(v0.z), tab_decode(v0.w));
+            d4[1] = make_uint4(tab_decode(v1.x), tab_decode(v1.y), tab_decode(v1.z), tab_decode(v1.w));
+            d4[2] = make_uint4(tab_decode(v2.x), tab_decode(v2.y), tab_decode(v2.z), tab_decode(v2.w));
+            d4[3] = make_uint4(tab_decode(v3.x), tab_decode(v3.y), tab_decode(v3.z), tab_decode(v3.w));
+        }
+        if (__all_sync(0xFFFFFFFFu, good)) break;
+        if (++spins > X.spin_limit) {
+            if (lane == 0) atomicExch(X.err, GDI_DEVERR_TIMEOUT);
+            ok = false;
+            break;
+        }
+        if ((spins & 63) == 0 && __any_sync(0xFFFFFFFFu, *(volatile int *)X.err != 0)) {
+            ok = false;
+            break;
+        }
+        __nanosleep(20);
+    }
+    __syncwarp();
+    return ok;
 }
 
 // the exact replay of one window by counting (|G - c| beyond the stored values), kept out of line
@@ -1302,8 +1339,6 @@ __global__ void __launch_bounds__(GB, 1) gdi_grid_sorted_kernel(GridArgs A)
     int32_t *Gc = reinterpret_cast<int32_t *>(S.misc);   // [8] class-start G of each replica
     unsigned char *cb = reinterpret_cast<unsigned char *>(X.tables);
     unsigned long long *exg = reinterpret_cast<unsigned long long *>(cb);
-    uint32_t *flag = reinterpret_cast<uint32_t *>(cb + chain_off_flag(Pb));
-    uint32_t *rflag = reinterpret_cast<uint32_t *>(cb + chain_off_rflag(Pb));
     int8_t *tabs = reinterpret_cast<int8_t *>(cb + chain_off_tab(Pb));
     int8_t *rtabs = reinterpret_cast<int8_t *>(cb + chain_off_rtab(Pb));
     const int NR = nruns(Pb);
@@ -1344,6 +1379,7 @@ __global__ void __launch_bounds__(GB, 1) gdi_grid_sorted_kernel(GridArgs A)
         __syncthreads();
         for (int c = 0; c < ncls; ++c) {
             ++epoch;
+            const uint32_t par = (epoch & 1u) << 7;        // parity of this class's table bytes
             int32_t a0, a1;
             int nwin;
             class_range(c, a0, a1, nwin);
@@ -1380,13 +1416,9 @@ __global__ void __launch_bounds__(GB, 1) gdi_grid_sorted_kernel(GridArgs A)
                     }
                 }
                 int8_t *dst = tabs + ((size_t)p * 8 + r) * NT;
-                dst[lane] = (int8_t)t0;
-                dst[lane + 32] = (int8_t)t1;
+                st_tab_byte(dst + lane, t0, par);
+                st_tab_byte(dst + lane + 32, t1, par);
             }
-            // the block barrier orders every warp's table stores before thread 0's release store,
-            // which publishes them at GPU scope (cumulative release)
-            __syncthreads();
-            if (threadIdx.x == 0) st_release_u32(flag + p, epoch);
             // ---- the last block of a run composes the run's block tables into the run table
             bool ok = true;
             if (leader) {
@@ -1394,9 +1426,9 @@ __global__ void __launch_bounds__(GB, 1) gdi_grid_sorted_kernel(GridArgs A)
                     const int r = warp;
                     int8_t *dt = walk + ((size_t)r * walk_slots(Pb) + NR + RUN) * NT;   // descent slots
                     const int cnt = p - run0;                 // blocks of the run before me
-                    ok = poll_flags(flag + run0, cnt, epoch, X);
+                    ok = fetch_valid(tabs + ((size_t)run0 * 8 + r) * NT, cnt, dt, nullptr, 0, nullptr,
+                                     (size_t)8 * NT, par, X);
                     if (ok) {
-                        fetch_tables(tabs + ((size_t)run0 * 8 + r) * NT, (size_t)8 * NT, cnt, dt);
                         int u0 = lane, u1 = lane + 32;
                         for (int k = 0; k < cnt; ++k) {
                             if (u0 >= 0) u0 = dt[k * NT + u0];
@@ -1410,12 +1442,10 @@ __global__ void __launch_bounds__(GB, 1) gdi_grid_sorted_kernel(GridArgs A)
                         u0 = u0 < 0 ? -1 : (u0 >= 32 ? x01 : x00);
                         u1 = u1 < 0 ? -1 : (u1 >= 32 ? x11 : x10);
                         int8_t *rd = rtabs + ((size_t)run * 8 + r) * NT;
-                        rd[lane] = (int8_t)u0;
-                        rd[lane + 32] = (int8_t)u1;
+                        st_tab_byte(rd + lane, u0, par);
+                        st_tab_byte(rd + lane + 32, u1, par);
                     }
                 }
-                __syncthreads();
-                if (threadIdx.x == 0) st_release_u32(rflag + run, epoch);
             }
             // ---- entering G: run tables of the runs before mine, then the block tables of my run
             if (warp < nrep) {
@@ -1425,11 +1455,14 @@ __global__ void __launch_bounds__(GB, 1) gdi_grid_sorted_kernel(GridArgs A)
                 int8_t *ws_own = ws_run + (size_t)NR * NT;                   // [RUN][64]
                 int8_t *ws_dsc = ws_own + (size_t)RUN * NT;                  // [RUN][64]
                 const int nown = p - run0;
-                if (ok) ok = poll_flags(rflag, run, epoch, X);
-                if (ok) ok = poll_flags(flag + run0, nown, epoch, X);
                 if (ok) {
-                    fetch_tables(rtabs + (size_t)r * NT, (size_t)8 * NT, run, ws_run);
-                    fetch_tables(tabs + ((size_t)run0 * 8 + r) * NT, (size_t)8 * NT, nown, ws_own);
+                    const int8_t *ra = rtabs + (size_t)r * NT, *ob = tabs + ((size_t)run0 * 8 + r) * NT;
+                    if (run + nown <= 32) {
+                        ok = fetch_valid(ra, run, ws_run, ob, nown, ws_own, (size_t)8 * NT, par, X);
+                    } else {
+                        ok = fetch_valid(ra, run, ws_run, nullptr, 0, nullptr, (size_t)8 * NT, par, X) &&
+                             fetch_valid(ob, nown, ws_own, nullptr, 0, nullptr, (size_t)8 * NT, par, X);
+                    }
                 }
                 int idx = NT / 2;          // lattice index of the running G, or -1 when off the lattice
                 int32_t gx = c0;           // the running G when off the lattice
@@ -1447,7 +1480,8 @@ __global__ void __launch_bounds__(GB, 1) gdi_grid_sorted_kernel(GridArgs A)
                     const int nidx = idx >= 0 ? (int)ws_run[q * NT + idx] : -1;
                     if (nidx >= 0) { idx = nidx; continue; }
                     // the run table cannot map the running G: walk the run block by block
-                    fetch_tables(tabs + ((size_t)q * RUN * 8 + r) * NT, (size_t)8 * NT, RUN, ws_dsc);
+                    ok = fetch_valid(tabs + ((size_t)q * RUN * 8 + r) * NT, RUN, ws_dsc, nullptr, 0, nullptr,
+                                     (size_t)8 * NT, par, X);
                     for (int k = 0; k < RUN && ok; ++k) block_step(ws_dsc + k * NT, q * RUN + k);
                     __syncwarp();
                 }
@@ -2015,7 +2049,7 @@ int gdi_launch_grid_anneal(const GdiDevProblem &P, const GdiDevRun &R, const Gdi
         cudaMemsetAsync(X.Gcls, 0, 8 * sizeof(int32_t), st);
         cudaMemsetAsync(X.bar, 0, 2 * sizeof(unsigned int), st);
         if (X.bar_start) set_word_kernel<<<1, 1, 0, st>>>(X.bar, X.bar_start);
-        if (sorted) cudaMemsetAsync(X.tables, 0, chain_off_tab(sms), st);
+        if (sorted) cudaMemsetAsync(X.tables, 0, chain_bytes(sms), st);
         GridArgs A;
         A.P = P;
         A.R = R;
