@@ -11,8 +11,9 @@
 //
 // Sorted-window variant (W <= 256, gdi_grid_sorted_kernel): a warp sorts each (window, replica)
 // group once, after which every member decides its own flip by one comparison; block tables are
-// published with release flags and each block finds its entering G by looking them up, so only
-// one grid barrier per class remains (described before the kernel).
+// published with the class parity in every byte and each block finds its entering G by looking
+// them up, so only one grid barrier per class remains (described before the kernel).  The local
+// fields are kept across classes and updated by the flips (atomic adds to the neighbours).
 //
 // Tabulated variant (W > 256, gdi_grid_anneal_kernel):
 //   * every window tabulates its map for G in [c - RT, c + RT] from two small histograms of its
@@ -24,7 +25,7 @@
 //     third barrier makes the class's spins visible to the next class.
 //
 // Grid barriers are sense/generation barriers on global counters with a bounded spin, and every
-// flag wait is bounded too: a block that waits too long sets the error word and the kernel returns
+// other wait (tables, exact G words) is bounded too: a block that waits too long sets the error word and the kernel returns
 // (GDI_ERR_TIMEOUT on the host).
 #include <cuda_runtime.h>
 #include <stdint.h>
