@@ -169,8 +169,8 @@ int gdi_last_launch(gdi_ctx *ctx, int32_t *path, int32_t *grid, int64_t *smem_by
                     int32_t *fallbacks);
 
 /* Failure-detection test hook (the paper has no counterpart).  The next gdi_anneal that takes the
- * grid-scale path starts with its grid barrier's arrival counter already past the trigger, set
- * from the host, so no barrier can complete -- a flag that no block will ever set.  Every block's
+ * grid-scale path starts with its grid barrier's gate word closed, set from the host, so no
+ * barrier can complete -- a flag that no block will ever clear.  Every block's
  * bounded wait then gives up after spin_limit polls (>= 1; each poll sleeps tens of ns), sets the
  * device error word and returns; the anneal reports GDI_ERR_TIMEOUT (from gdi_get_results and
  * the other synchronising calls).  Nothing faults, traps or hangs, the context stays usable, and

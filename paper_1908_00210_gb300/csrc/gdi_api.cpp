@@ -713,7 +713,7 @@ int gdi_anneal(gdi_ctx *c, const gdi_schedule *S, const gdi_run *run)
         if (e == cudaSuccess) e = c->g_rhist.alloc((size_t)8 * (2 * D + 1));
         if (e == cudaSuccess) e = c->g_rties.alloc((size_t)8 * 152 * 4);
         if (e == cudaSuccess) e = c->g_rparams.alloc(32);
-        if (e == cudaSuccess) e = c->g_bar.alloc(2);
+        if (e == cudaSuccess) e = c->g_bar.alloc(4);
         if (e == cudaSuccess && c->W <= 256) e = c->g_hfield.alloc((size_t)2 * c->N);
         if (e != cudaSuccess) return fail(GDI_ERR_OOM, "device allocation failed (grid scratch)");
         cudaMemsetAsync(c->g_err.p, 0, sizeof(int32_t), st);

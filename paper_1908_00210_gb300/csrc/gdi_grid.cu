@@ -100,32 +100,31 @@ struct GridArgs {
 };
 
 // ---------------------------------------------------------------------------------------------
-// bounded grid barrier; returns false (and the caller must return) if any block timed out
+// bounded grid barrier; returns false (and the caller must return) if any block timed out.  The
+// arrival counter only grows: barrier k of a launch completes when it reaches k * gridDim.x, so the
+// last arrival has nothing left to do (no reset, no generation word) and the waiters see the count
+// one round trip after it lands.  bar[2] is a gate the failure-detection hook closes: while it is
+// set no barrier completes and every wait runs into its bound.
 __device__ bool grid_sync(const GdiGridScratch &X)
 {
     __syncthreads();
     __shared__ int ok;
     if (threadIdx.x == 0) {
-        volatile unsigned int *gen = X.bar + 1;
-        const unsigned int g0 = *gen;
+        unsigned long long *cnt = reinterpret_cast<unsigned long long *>(X.bar);
+        volatile unsigned int *gate = X.bar + 2;
         __threadfence();
-        const unsigned int arrived = atomicAdd(X.bar, 1u);
+        const unsigned long long old = atomicAdd(cnt, 1ull);
+        const unsigned long long target = (old / gridDim.x + 1) * gridDim.x;
         int good = 1;
-        if (arrived == gridDim.x - 1) {
-            atomicExch(X.bar, 0u);
-            __threadfence();
-            atomicAdd((unsigned int *)gen, 1u);
-        } else {
-            long long spins = 0;
-            while (*gen == g0) {
-                if (++spins > X.spin_limit) {
-                    atomicExch(X.err, GDI_DEVERR_TIMEOUT);
-                    good = 0;
-                    break;
-                }
-                if (*(volatile int *)X.err) { good = 0; break; }
-                __nanosleep(64);
+        long long spins = 0;
+        while (*(volatile unsigned long long *)cnt < target || *gate) {
+            if (++spins > X.spin_limit) {
+                atomicExch(X.err, GDI_DEVERR_TIMEOUT);
+                good = 0;
+                break;
             }
+            if (*(volatile int *)X.err) { good = 0; break; }
+            __nanosleep(64);
         }
         __threadfence();
         if (*(volatile int *)X.err) good = 0;
@@ -2048,8 +2047,8 @@ int gdi_launch_grid_anneal(const GdiDevProblem &P, const GdiDevRun &R, const Gdi
         const int nrep = P.replicas - g0 < 8 ? P.replicas - g0 : 8;
         pack_kernel<<<pg, 256, 0, st>>>(spins, P.N, g0, nrep, X.packed);
         cudaMemsetAsync(X.Gcls, 0, 8 * sizeof(int32_t), st);
-        cudaMemsetAsync(X.bar, 0, 2 * sizeof(unsigned int), st);
-        if (X.bar_start) set_word_kernel<<<1, 1, 0, st>>>(X.bar, X.bar_start);
+        cudaMemsetAsync(X.bar, 0, 4 * sizeof(unsigned int), st);
+        if (X.bar_start) set_word_kernel<<<1, 1, 0, st>>>(X.bar + 2, 1u);
         if (sorted) cudaMemsetAsync(X.tables, 0, chain_bytes(sms), st);
         GridArgs A;
         A.P = P;

@@ -34,7 +34,7 @@ struct GdiGridScratch {
                                      // words, table-ready flags and [P][8][64] byte tables
     int32_t *gin;                    // [P][8] exact G entering every block's windows
     int32_t *Gcls;                   // [8] G at class start / after the class
-    unsigned int *bar;               // [2] grid barrier: arrival count, generation
+    unsigned int *bar;               // [4] grid barrier: 64-bit arrival count, gate, unused
     int32_t *err;                    // [1] device error word
     int32_t *status;                 // [16] diagnostics: exact fallbacks per replica
     int32_t *rhist;                  // [8][2*max_degree+1] repair key histogram
@@ -44,7 +44,7 @@ struct GdiGridScratch {
     unsigned long long *hfield;      // [N][2] maintained local fields of the replica group (the
                                      // sorted-window path), or null: fields gathered every class
     long long spin_limit;            // polls before a device wait gives up (error word set)
-    unsigned int bar_start;          // initial barrier arrival count (0; test hook: blocks)
+    unsigned int bar_start;          // nonzero: the barrier's gate starts closed (test hook)
 };
 
 // One annealing call.

@@ -107,8 +107,8 @@ def test_grid_ba_1m_first_sweeps(gdi):
 
 
 def test_bounded_waits_report_timeout_and_context_recovers(gdi):
-    """Failure detection without a GPU fault: the host starts the grid barrier's arrival counter
-    past its trigger, so no block's wait can end; every wait gives up after a short bounded poll,
+    """Failure detection without a GPU fault: the host closes the grid barrier's gate word before
+    the launch, so no block's wait can end; every wait gives up after a short bounded poll,
     the anneal reports GDI_ERR_TIMEOUT, and the same context then anneals normally (bit-exact)."""
     g = barabasi_albert(20000, 5, 60)
     ann = gdi.Annealer(g, A=1, B=4, W=64, replicas=2)
