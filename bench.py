@@ -35,7 +35,7 @@ WORKLOADS = {
                     sweeps=500, t0=12.0, t1=0.2, seed=1,
                     # traffic: dram__bytes_read.sum + dram__bytes_write.sum of one 500-sweep launch
                     # of gdi_grid_sorted_kernel<8> (ncu, profiles/gdi_grid_sorted_kernel_ba1m_r8.md)
-                    roofline=dict(bound="hbm", bytes_per_update=56, traffic=50085888 + 2045440)),
+                    roofline=dict(bound="hbm", bytes_per_update=56, traffic=50145024 + 2043904)),
     # 2-D torus 100 x 100, +-1 weights, checkerboard colouring, 64 replicas, 5000 sweeps
     "torus100_r64": dict(kind="torus", L=100, gseed=2002, A=1, B=4, W=1024, replicas=64,
                          sweeps=5000, t0=12.0, t1=0.2, seed=1,
