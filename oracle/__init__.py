@@ -5,13 +5,16 @@ It wraps oracle/gdi_oracle.c (plain sequential C, built with gcc) through ctypes
 code with the CUDA library in paper_1908_00210_gb300/.
 
 Parity status of each function (what pins it, apart from itself):
-  philox4x32_10      Triton's library Philox (CPU interpreter) and cuRAND's Philox4_32_10 (GPU).
+  philox4x32_10      Triton's library Philox run by its CPU interpreter; uniformity and avalanche.
   greedy_color       properness + first-fit minimality checked by brute force in the tests.
   table              closed forms exp(-dE/T) and the P_f probabilities of Alg. 2/3.
   energy / cut       Eq. 3 with dense couplings J_ij = B w_ij / 2 - 2A (dense numpy), brute force.
-  anneal             W = 1 reduces to textbook single-spin Metropolis with the energy recomputed
-                     from scratch (tests), invariants (tracked G and cut equal recomputation),
-                     brute-force optimum bound on n <= 20.
+  anneal             every flip decided by u < thr[s][clamp(dE at the running G)], with dE from
+                     Eq. 4-6; W = 1 reduces to textbook single-spin Metropolis with the energy
+                     recomputed from scratch (tests); W > 1 replayed with flip thresholds found by
+                     scanning G with the energy recomputed from its definition, in both table
+                     modes, for several replica and instance words; invariants (tracked G and cut
+                     equal recomputation); brute-force optimum bound on n <= 20.
   bruteforce         exhaustive enumeration, checked on graphs with known bisection widths.
 """
 from __future__ import annotations
@@ -75,6 +78,7 @@ class _Out(C.Structure):
         ("invariant_failures", C.c_int64),
         ("num_colors", C.c_int32),
         ("do_repair", C.c_int32),
+        ("decision_mismatches", C.c_int64),
     ]
 
 
@@ -195,10 +199,13 @@ def anneal(g, *, A: int = 1, B: int = 1, W: int = 0, mode: int = METROPOLIS, t0:
                 seed & 0xFFFFFFFFFFFFFFFF, instance, replicas, first_sweep, last_sweep,
                 1 if check_invariants else 0, first_replica)
     O = _Out(_p(spins), 1 if init is not None else 0, _p(raw_G), _p(final_G), _p(raw_cut),
-             _p(final_cut), _p(dig), _p(gtr), _p(ctr), 0, 0, 1 if repair else 0)
+             _p(final_cut), _p(dig), _p(gtr), _p(ctr), 0, 0, 1 if repair else 0, 0)
     rc = lib().oracle_anneal(C.byref(P), C.byref(O))
     if rc != 0:
         raise ValueError(f"oracle_anneal failed with code {rc}")
+    if O.decision_mismatches:
+        raise AssertionError(f"oracle: {O.decision_mismatches} flips where the threshold order key "
+                             "disagreed with the acceptance test")
     return AnnealResult(spins, raw_G, final_G, raw_cut, final_cut, dig, gtr, ctr,
                         int(O.invariant_failures), int(O.num_colors))
 

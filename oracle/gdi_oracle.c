@@ -33,7 +33,10 @@
  *       ascending on ties), then the spins that were -1, sorted by gamma' descending (rank
  *       ascending); on odd sweeps the -1 group goes first.  gamma is the smallest G at which the
  *       spin's draw accepts the flip, so the spins that most want to flip get to the running G
- *       first, the way the earliest atomics would.
+ *       first, the way the earliest atomics would.  gamma only fixes that order: each flip is
+ *       decided from its definition, the draw against the table entry of the energy change at
+ *       the running G, and the run counts any flip where "G >= gamma" would have said otherwise
+ *       (there must be none).
  *   R3  One draw per spin per sweep merges "argmin" and "flip with probability P_f" into a single
  *       Bernoulli decision with the same probabilities (flip w.p. 1-P_f if dE<0, 1/2 if dE=0, P_f
  *       if dE>0); "flip iff u <= P_f" (Section 5.2) becomes u32 < floor(P_f 2^32) + 1.
@@ -294,6 +297,8 @@ typedef struct {
     int64_t invariant_failures;
     int32_t num_colors;
     int32_t do_repair;
+    int64_t decision_mismatches; /* flips where "G >= gamma" (the order key) disagreed with the
+                                    acceptance test u < thr[clamp(dE)] that decides them; 0 */
 } oracle_out;
 
 static int64_t weight_of(const oracle_params *p, int64_t e)
@@ -385,11 +390,12 @@ int oracle_anneal(const oracle_params *p, oracle_out *o)
     int8_t *s0 = (int8_t *)malloc((size_t)n);                         /* window start */
     int64_t *hbuf = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
     int64_t *gbuf = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+    uint32_t *ubuf = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)n); /* this sweep's draws */
     sort_item *items = (sort_item *)malloc(sizeof(sort_item) * (size_t)n);
     int32_t *cls_lo = (int32_t *)malloc(sizeof(int32_t) * ((size_t)n + 1));
-    if (!thr || !color || !rank || !vert || !s || !so || !s0 || !hbuf || !gbuf || !items || !cls_lo) {
+    if (!thr || !color || !rank || !vert || !s || !so || !s0 || !hbuf || !gbuf || !ubuf || !items || !cls_lo) {
         free(thr); free(color); free(rank); free(vert); free(s); free(so); free(s0); free(hbuf);
-        free(gbuf); free(items); free(cls_lo);
+        free(gbuf); free(ubuf); free(items); free(cls_lo);
         return ORC_ERR_OOM;
     }
     int rc = ORC_OK;
@@ -478,6 +484,7 @@ int oracle_anneal(const oracle_params *p, oracle_out *o)
                         hbuf[r] = h;
                         const uint32_t u = draw_word(p->seed, (uint32_t)(r >> 2), (uint32_t)sw,
                                                      (uint32_t)p->instance, (uint32_t)(p->first_replica + rep), r & 3);
+                        ubuf[r] = u;
                         const int64_t Es = estar(row, ecap, u);
                         gbuf[r] = (s[r] > 0) ? gamma_plus(h, Es, p->A, p->B)
                                              : gamma_minus(h, Es, p->A, p->B);
@@ -497,7 +504,16 @@ int oracle_anneal(const oracle_params *p, oracle_out *o)
                         qsort(items, (size_t)m, sizeof(sort_item), cmp_item);
                         for (int32_t t = 0; t < m; ++t) {
                             const int32_t r = items[t].rank;
-                            const int flip = plus_group ? (G >= gbuf[r]) : (G <= gbuf[r]);
+                            /* the decision itself, from its definition: the energy change of
+                             * flipping r at the running G (Eq. 4-6, R1) looked up in this sweep's
+                             * row and compared with the draw (Alg. 3's acceptance, R3/R6) */
+                            const int64_t dE = (int64_t)p->B * s[r] * hbuf[r]
+                                             + 4 * (int64_t)p->A * (1 - (int64_t)s[r] * G);
+                            const int64_t kc = (dE < -ecap ? -ecap : (dE > ecap ? ecap : dE)) + ecap;
+                            const int flip = (uint64_t)ubuf[r] < row[kc];
+                            /* gamma only orders the group (R2); it must say the same */
+                            const int by_gamma = plus_group ? (G >= gbuf[r]) : (G <= gbuf[r]);
+                            if (flip != by_gamma) o->decision_mismatches++;
                             if (flip) {
                                 cut += (int64_t)s[r] * hbuf[r];   /* change of the cut: s_i h_i */
                                 G -= 2 * (int64_t)s[r];
@@ -559,7 +575,7 @@ int oracle_anneal(const oracle_params *p, oracle_out *o)
     }
 done:
     free(thr); free(color); free(rank); free(vert); free(s); free(so); free(s0); free(hbuf);
-    free(gbuf); free(items); free(cls_lo);
+    free(gbuf); free(ubuf); free(items); free(cls_lo);
     return rc;
 }
 

@@ -115,3 +115,130 @@ def test_adam_step_closed_form():
     g = np.array([0.3, -2.0, 1e-3])
     p1, m, v = mpnn.adam_step(p, g, np.zeros(3), np.zeros(3), 0.01, 0.9, 0.999, 1e-12, 1)
     assert np.allclose(p1, p - 0.01 * np.sign(g), atol=1e-9)
+
+
+# ------------------------------------------------------------------ closed-form pins ----------
+def _star(m):
+    from gdi_synth import star_graph
+    return star_graph(m + 1)            # vertex 0 is the hub, 1..m the leaves
+
+
+def test_mean_aggregate_closed_forms():
+    """D^-1 A X: on K_n every vertex gets (sum - own) / (n - 1); on a star the hub gets the mean of
+    the leaves and every leaf the hub's row; an isolated vertex gets 0."""
+    from gdi_synth import from_edges
+    rng = np.random.default_rng(11)
+    n = 7
+    u, v = np.triu_indices(n, 1)
+    k = from_edges(n, u, v)
+    X = rng.standard_normal((n, 3))
+    Y = mpnn.mean_aggregate(k.row_ptr, k.col, X)
+    assert np.allclose(Y, (X.sum(axis=0) - X) / (n - 1), rtol=0, atol=1e-13)
+    s = _star(5)
+    X = rng.standard_normal((6, 2))
+    Y = mpnn.mean_aggregate(s.row_ptr, s.col, X)
+    assert np.allclose(Y[0], X[1:].mean(axis=0), atol=1e-13)
+    assert np.allclose(Y[1:], np.broadcast_to(X[0], (5, 2)), atol=1e-13)
+    iso = from_edges(3, np.array([0]), np.array([1]))     # vertex 2 has no neighbour
+    Y = mpnn.mean_aggregate(iso.row_ptr, iso.col, np.ones((3, 1)))
+    assert Y[2, 0] == 0.0 and Y[0, 0] == 1.0
+
+
+def test_mean_aggregate_transpose_is_the_adjoint():
+    """<D^-1 A X, Y> = <X, (D^-1 A)^T Y> for any X, Y (the transposed operator of the backward)."""
+    g = erdos_renyi(60, 0.08, 12)
+    rng = np.random.default_rng(2)
+    X = rng.standard_normal((g.n, 4))
+    Y = rng.standard_normal((g.n, 4))
+    lhs = np.sum(mpnn.mean_aggregate(g.row_ptr, g.col, X) * Y)
+    rhs = np.sum(X * mpnn.mean_aggregate_T(g.row_ptr, g.col, Y))
+    assert lhs == pytest.approx(rhs, rel=1e-12)
+
+
+@pytest.mark.parametrize("n,k,t", [(12, 1, 1), (12, 3, 5), (31, 2, 40), (16, 8, 3)])
+def test_lazy_walk_multiplies_cycle_fourier_modes(n, k, t):
+    """On the cycle C_n, D^-1/2 A D^-1/2 = A / 2 has the Fourier modes cos(2 pi k i / n + phi) as
+    eigenvectors with eigenvalue cos(2 pi k / n); t lazy steps multiply them by
+    ((1 + cos(2 pi k / n)) / 2)^t."""
+    from gdi_synth import from_edges
+    i = np.arange(n)
+    c = from_edges(n, i, (i + 1) % n)
+    theta = 2 * np.pi * k / n
+    X = np.stack([np.cos(theta * i + 0.3), np.sin(theta * i - 1.1)], axis=1)
+    Y = X.copy()
+    for _ in range(t):
+        Y = mpnn.lazy_walk(c.row_ptr, c.col, Y)
+    assert np.allclose(Y, X * ((1 + np.cos(theta)) / 2) ** t, rtol=0, atol=1e-12)
+
+
+def test_lazy_walk_star_eigenvectors():
+    """Star K_{1,m} (not regular): D^-1/2 A D^-1/2 fixes sqrt(deg) (eigenvalue 1), maps
+    sqrt(deg) * (+1 hub, -1 leaves) to its negative (eigenvalue -1, so a lazy step gives 0), and
+    annihilates a difference of two leaves (eigenvalue 0, a lazy step halves it)."""
+    m = 6
+    s = _star(m)
+    sq = np.sqrt(np.diff(s.row_ptr).astype(np.float64))
+    top = sq[:, None]
+    bip = (sq * np.where(np.arange(m + 1) == 0, 1.0, -1.0))[:, None]
+    dif = np.zeros((m + 1, 1))
+    dif[1], dif[2] = 1.0, -1.0
+    assert np.allclose(mpnn.lazy_walk(s.row_ptr, s.col, top), top, atol=1e-13)
+    assert np.allclose(mpnn.lazy_walk(s.row_ptr, s.col, bip), 0.0, atol=1e-13)
+    assert np.allclose(mpnn.lazy_walk(s.row_ptr, s.col, dif), 0.5 * dif, atol=1e-13)
+
+
+def _golden_mpnn():
+    import os
+    fx = {"w": [], "b": [], "v": []}
+    for line in open(os.path.join(os.path.dirname(__file__), "golden", "mpnn_path4_forward.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        k, *vals = line.split()
+        if k in ("w", "b", "v"):
+            fx[k].append(vals)
+        else:
+            fx[k] = vals
+    return fx
+
+
+def test_forward_hand_derived_path4():
+    """tests/golden/mpnn_path4_forward.txt: a 3-layer forward pass worked out by hand (mean
+    aggregation, self and neighbour weights, biases, ReLU clipping, output layer, rounding)."""
+    from gdi_synth import from_edges
+    fx = _golden_mpnn()
+    eu, ev = zip(*[tuple(map(int, e.split("-"))) for e in fx["edges"]])
+    g = from_edges(4, np.array(eu), np.array(ev))
+    _, total = mpnn.param_layout()
+    P = mpnn.unpack(np.zeros(total))
+    P = {k: v.copy() for k, v in P.items()}
+    for name, i, j, val in fx["w"]:
+        P[name][int(i), int(j)] = float(val)
+    for name, i, val in fx["b"] + fx["v"]:
+        P[name][int(i)] = float(val)
+    X = np.zeros((4, mpnn.FIN))
+    X[:, 0] = list(map(float, fx["x0"]))
+    X[:, 1] = list(map(float, fx["x1"]))
+    z, cache = mpnn.forward(P, g.row_ptr, g.col, X)
+    for (l, ch) in ((1, 0), (1, 1), (1, 2), (1, 3), (2, 0), (2, 1), (3, 5), (3, 6)):
+        assert cache[l - 1][2][:, ch].tolist() == list(map(float, fx[f"h{l}_{ch}"])), (l, ch)
+    others = np.ones(mpnn.HID, bool)
+    others[[5, 6]] = False
+    assert np.all(cache[2][2][:, others] == 0)
+    assert z.tolist() == list(map(float, fx["z"]))
+    s = mpnn.round_balanced(np.array([0, 4]), z.astype(np.float32))
+    assert s.tolist() == list(map(int, fx["spins"]))
+    # the same numbers through the float32 -> BF16 path the GPU uses (every value is BF16-exact)
+    flat = mpnn.flat_grads(P).astype(np.float32)
+    z2, _ = mpnn.forward(mpnn.effective_params(flat), g.row_ptr, g.col, X)
+    assert z2.tolist() == z.tolist()
+
+
+@pytest.mark.parametrize("c,lam", [(0.0, 0.3), (0.7, 0.0), (-1.3, 0.25)])
+def test_loss_closed_form_for_constant_logits(c, lam):
+    """Balanced labels and constant logits z = c: both signs give (softplus(c) + softplus(-c)) / 2
+    = log(2 cosh(c / 2)), and the balance term is lam tanh(c)^2 (z = 0: log 2)."""
+    gp = np.array([0, 6, 14], dtype=np.int64)
+    y = np.array([1, -1, 1, -1, -1, 1] + [1, 1, -1, -1, 1, -1, 1, -1], dtype=np.int8)
+    z = np.full(14, c)
+    L, _, _ = mpnn.loss(gp, z, y, lam)
+    assert L == pytest.approx(np.log(2 * np.cosh(c / 2)) + lam * np.tanh(c) ** 2, rel=1e-12)

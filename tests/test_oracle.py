@@ -257,20 +257,31 @@ def _gamma_bruteforce(g, A, B, s, v, u, row, ecap, sign):
     return 10 ** 9 if acc[-1] else (Gs[len(Gs) - 1 - np.argmax(acc[::-1])] if acc.any() else -10 ** 9)
 
 
-@pytest.mark.parametrize("W,seed", [(0, 1), (3, 2), (5, 3)])
-def test_window_canonical_order_bruteforce(W, seed):
+@pytest.mark.parametrize("mode,W,A,seed,inst,rep", [
+    (oracle.METROPOLIS, 0, 1, 1, 0, 0), (oracle.METROPOLIS, 3, 1, 2, 0, 0),
+    (oracle.METROPOLIS, 5, 1, 3, 0, 0), (oracle.METROPOLIS, 4, 2, 4, 3, 5),
+    (oracle.METROPOLIS, 6, 0, 5, 1, 2), (oracle.PAPER_PF, 0, 1, 6, 0, 0),
+    (oracle.PAPER_PF, 4, 2, 7, 2, 3), (oracle.PAPER_PF, 7, 0, 8, 0, 6),
+    (oracle.PAPER_PF, 3, 1, 9, 5, 1)])
+def test_window_canonical_order_bruteforce(mode, W, A, seed, inst, rep):
     """Reading R2 replayed with thresholds found by brute force: within a window the +1 group (by
-    gamma asc, rank asc) and the -1 group (by gamma' desc, rank asc) each see the running G."""
-    g = erdos_renyi(20, 0.3, 70 + seed)
-    A, B, M = 1, 2, 6
-    ecap, thr = oracle.table(oracle.METROPOLIS, 3.0, 0.5, 0, 0, M)
+    gamma asc, rank asc) and the -1 group (by gamma' desc, rank asc) each see the running G, and
+    every flip is the acceptance test at that G.  Both table modes (Metropolis; the paper's P_f of
+    Algorithm 3, whose thresholds are mostly the +-infinite sentinels), windows W > 1, A = 0 (no
+    decision depends on G), and replica and instance words other than 0."""
+    g = erdos_renyi(20, 0.3, 70 + seed, signed=(seed % 3 == 0))
+    B, M = 2, 6
+    sk = dict(mode=mode, t0=3.0, t1=0.5, pf0=0.3, pf1=0.05)
+    ecap, thr = oracle.table(mode, 3.0, 0.5, 0.3, 0.05, M)
     color = oracle.greedy_color(g)
     vert = _rank_order(g, color)
     rank = np.empty(g.n, dtype=np.int64)
     rank[vert] = np.arange(g.n)
     classes = np.unique(color)
-    prev = oracle.anneal(g, A=A, B=B, W=W, t0=3.0, t1=0.5, sweeps=M, seed=seed, last_sweep=1, repair=False)
+    kw = dict(A=A, B=B, W=W, sweeps=M, seed=seed, instance=inst, first_replica=rep, repair=False, **sk)
+    prev = oracle.anneal(g, last_sweep=1, **kw)
     s = prev.spins[0].copy()
+    flips = 0
     for sw in range(1, M):
         for c in classes:
             members = vert[color[vert] == c]
@@ -280,7 +291,7 @@ def test_window_canonical_order_bruteforce(W, seed):
                 s0 = s.copy()
                 gam = {}
                 for v in win:
-                    u = _draw(seed, int(rank[v]), sw, 0, 0)
+                    u = _draw(seed, int(rank[v]), sw, inst, rep)
                     gam[v] = _gamma_bruteforce(g, A, B, s0, v, u, thr[sw], ecap, int(s0[v]))
                 G = int(s.sum())
                 groups = [+1, -1] if sw % 2 == 0 else [-1, +1]
@@ -291,12 +302,12 @@ def test_window_canonical_order_bruteforce(W, seed):
                         if (grp > 0 and G >= gam[v]) or (grp < 0 and G <= gam[v]):
                             s[v] = -s[v]
                             G -= 2 * grp
-        nxt = oracle.anneal(g, A=A, B=B, W=W, t0=3.0, t1=0.5, sweeps=M, seed=seed,
-                            init=prev.spins if sw == 1 else cur, first_sweep=sw, last_sweep=sw + 1,
-                            repair=False)
-        cur = nxt.spins
+                            flips += 1
+        nxt = oracle.anneal(g, init=prev.spins, first_sweep=sw, last_sweep=sw + 1, **kw)
         prev = nxt
-        assert np.array_equal(cur[0], s), f"sweep {sw}"
+        assert np.array_equal(nxt.spins[0], s), f"sweep {sw}"
+        assert nxt.G_trace[0, sw] == int(s.sum())
+    assert flips > 0
 
 
 @pytest.mark.parametrize("W", [0, 1, 7, 64])
