@@ -113,8 +113,14 @@ typedef struct {
 } gdi_run;
 
 /* Build a context: validate the CSR (symmetric, no self-loops, no duplicates, weights +-1),
- * colour it (or check the given colouring), relabel every instance into rank order (colour asc,
- * vertex id asc), and copy it to the current CUDA device.  Host-side preprocessing; blocking. */
+ * colour it (or check the given colouring), relabel every instance into rank order, and copy it to
+ * the current CUDA device.  Rank order: the vertices of an instance sorted by colour ascending,
+ * then inside each colour class by splitmix64(local vertex id) ascending (splitmix64 = the
+ * finaliser of Steele, Lea and Flood, OOPSLA'14: z += 0x9E3779B97F4A7C15; z = (z ^ z>>30) *
+ * 0xBF58476D1CE4E5B9; z = (z ^ z>>27) * 0x94D049BB133111EB; z ^= z>>31), a fixed pseudo-random
+ * order inside the class; gdi_rank_space returns it.  This is the update order of the deterministic
+ * reading of Algorithm 3 (Section 5.3): classes in order, each class in windows of W consecutive
+ * ranks.  Host-side preprocessing; blocking. */
 int gdi_create(gdi_ctx **out, const gdi_graph *graph, const gdi_model *model);
 
 /* Anneal every replica of every instance with Algorithm 3, serialised deterministically: colour
@@ -135,10 +141,16 @@ int gdi_get_spins(gdi_ctx *ctx, int8_t *out, int32_t out_mem);
 int gdi_get_results(gdi_ctx *ctx, int32_t *raw_G, int32_t *final_G, int64_t *raw_cut,
                     int64_t *final_cut);
 
-/* Cut after repair of one (instance, replica). */
+/* Cut after repair of one (instance, replica): the sum of w_ij over the edges whose ends lie on
+ * different sides, i.e. the cut term of Eq. 6 without its factor B (Section 4.1), which for unit
+ * weights is the number of crossing edges that Table 1 reports (Section 6.2).  Host pointer;
+ * GDI_ERR_INVALID_ARG for an index out of range, GDI_ERR_NOT_ANNEALED before any anneal.
+ * Synchronises the run stream. */
 int gdi_cut(gdi_ctx *ctx, int32_t instance, int32_t replica, int64_t *cut_out);
 
-/* Magnetisation G = |V1| - |V2| before (raw) and after the repair of one (instance, replica). */
+/* Magnetisation G = sum_i s_i = |V1| - |V2| of one (instance, replica) before (raw) and after the
+ * repair: the quantity Eq. 5 penalises and the balance column of Table 1 (Section 6.2).  After the
+ * repair |G| = n mod 2.  Host pointers, either may be NULL; errors as gdi_cut.  Synchronises. */
 int gdi_balance(gdi_ctx *ctx, int32_t instance, int32_t replica, int32_t *raw_G, int32_t *final_G);
 
 /* Per-sweep trace of the last gdi_anneal with GDI_FLAG_TRACE: [q * replicas + r][sweeps] arrays of
@@ -190,6 +202,29 @@ int gdi_kernel_time(gdi_ctx *ctx, float *ms, int32_t *launches);
  * the largest degree, and the E_cap of the last schedule (0 before any anneal). */
 int gdi_info(gdi_ctx *ctx, int32_t *num_classes, int32_t *max_degree, int32_t *ecap);
 
+/* Rank-space layout of one graph (num_instances = 1), computed on the host exactly as gdi_create
+ * computes it, in the form gdi_anneal_static takes: validation and colouring as gdi_create (greedy
+ * first-fit when graph->color is NULL), then
+ *   vert_of   [n]      the original vertex at rank r (rank order as described at gdi_create);
+ *   row_ptr   [n + 1]  CSR offsets of the relabelled graph;
+ *   col       [nnz]    neighbour rank | 0x80000000 when the edge weight is -1;
+ *   class_ptr [num_classes + 1] rank boundaries of the colour classes (room for n + 1 entries);
+ *   max_class, max_degree (may be NULL).
+ * All host arrays owned by the caller.  Errors as gdi_create.  No device work. */
+int gdi_rank_space(const gdi_graph *graph, int32_t *vert_of, int64_t *row_ptr, uint32_t *col,
+                   int32_t *class_ptr, int32_t *num_classes, int32_t *max_class,
+                   int32_t *max_degree);
+
+/* Threshold table of a schedule, built on the host as gdi_anneal builds it ("reduce P_f" of
+ * Algorithms 2 and 3 becomes one table row per sweep, Section 5.2), in the form gdi_anneal_static
+ * takes.  Metropolis row s holds floor(exp(-dE / T_s) 2^32) for dE = 1, 2, ... while non-zero,
+ * T_s = t0 (t1/t0)^(s/(M-1)), temp[s] = T_s; paper row s holds 2^32 - p_s, 2^31, p_s with
+ * p_s = floor(P_f,s 2^32) + 1 (a flip iff u <= P_f) and temp[s] = 0.  With tab == NULL only *tab_len
+ * and *max_row are returned (a size query); otherwise tab [tab_cap >= *tab_len], tab_off
+ * [sweeps + 1] and temp [sweeps] are filled.  Host arrays owned by the caller. */
+int gdi_build_table(const gdi_schedule *schedule, uint32_t *tab, int64_t tab_cap, int64_t *tab_len,
+                    int32_t *tab_off, float *temp, int32_t *max_row);
+
 /* ---- Allocation-free sweep (the paper has no counterpart) -----------------------------------
  * For callers that cannot allocate device memory while they run: code whose device memory belongs
  * to another allocator (a framework's caching pool or a fixed arena) or that must not grow its
@@ -200,13 +235,14 @@ int gdi_info(gdi_ctx *ctx, int32_t *num_classes, int32_t *max_degree, int32_t *e
  * device array of about 1.4 MB that every GPU which loads libgdi.so keeps until the process exits.
  *
  * Inputs (device pointers, current device, read only):
- *   row_ptr   [n + 1] int64 CSR offsets of the graph relabelled in rank order (vertices sorted by
- *             colour, then id); col [row_ptr[n]] neighbour rank | 0x80000000 when the weight is -1.
+ *   row_ptr   [n + 1] int64 CSR offsets of the graph relabelled in rank order (the order described
+ *             at gdi_create: colour, then splitmix64 of the vertex id -- gdi_rank_space computes
+ *             it; any other order anneals in a different order and gives different results from
+ *             gdi_anneal); col [row_ptr[n]] neighbour rank | 0x80000000 when the weight is -1.
  *   class_ptr [num_classes + 1] rank boundaries of the colour classes (0 ... n); max_class is the
  *             largest class, max_degree the largest row length.
- *   tab, tab_off [sweeps + 1], temp [sweeps]: the threshold table (Metropolis: row s holds
- *             floor(exp(-dE / T_s) 2^32) for dE = 1, 2, ... while non-zero, temp[s] = T_s; paper
- *             mode: row s holds 2^32 - p_s, 2^31, p_s), max_row its longest row.
+ *   tab, tab_off [sweeps + 1], temp [sweeps]: the threshold table as gdi_build_table returns it,
+ *             max_row its longest row.
  *   A, B, W, mode, sweeps, [first_sweep, last_sweep) (last_sweep <= 0 = sweeps), seed: as in
  *   gdi_model / gdi_schedule / gdi_run; replicas 1..8 draw Philox counters (rank/4, sweep, 0, r).
  * In/out: spins [replicas][n] int8 (+1/-1) in rank order, annealed in place (no repair).
@@ -219,7 +255,13 @@ int gdi_info(gdi_ctx *ctx, int32_t *num_classes, int32_t *max_degree, int32_t *e
  * the one array, which keeps the previous call's contents (the call clears what must start at
  * zero): calls whose work overlaps on the GPU race with each other, so serialise them (one stream,
  * or events).  If a grid barrier wait ever ran out, the kernel stops early and the spins are those
- * of the interrupted sweep. */
+ * of the interrupted sweep.
+ * Input checks: the sizes and arrays above come from the caller, so before the anneal the call
+ * enqueues checks that row_ptr starts at 0 with rows of at most max_degree entries, that every
+ * neighbour rank is below n and outside its row's colour class, that class_ptr runs monotonically
+ * from 0 to n with no class above max_class, and that every table row of the sweep range fits
+ * max_row.  A failed check launches no sweep work: spins stay as they were and G_out is undefined.
+ * Symmetry of the CSR is not checked.  gdi_anneal_static_status reports the outcome. */
 #define GDI_STATIC_MAX_VERTICES (1 << 20)
 #define GDI_STATIC_MAX_BLOCKS 160
 int gdi_anneal_static(int32_t n, const int64_t *row_ptr, const uint32_t *col, int32_t num_classes,
@@ -229,7 +271,14 @@ int gdi_anneal_static(int32_t n, const int64_t *row_ptr, const uint32_t *col, in
                       int32_t first_sweep, int32_t last_sweep, uint64_t seed, int32_t replicas,
                       int8_t *spins, int32_t *G_out, void *stream);
 
-/* Free the context and its device buffers (synchronises the run stream first). */
+/* Outcome of the last gdi_anneal_static on the current device, enqueued on `stream` after it: a
+ * one-thread kernel writes GDI_OK, GDI_ERR_INVALID_ARG (an input check failed) or GDI_ERR_TIMEOUT
+ * (a bounded device wait ran out) into *status, which must be device-accessible memory (device
+ * memory, or mapped pinned host memory).  Allocates nothing; the paper has no counterpart. */
+int gdi_anneal_static_status(int32_t *status, void *stream);
+
+/* Free the context and its device buffers (synchronises the run stream first).  Library
+ * housekeeping: the paper has no counterpart.  NULL is allowed and does nothing. */
 void gdi_destroy(gdi_ctx *ctx);
 
 /* Static description of an error code. */

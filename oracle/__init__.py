@@ -90,6 +90,7 @@ def lib():
     if _lib is None:
         L = C.CDLL(build())
         L.oracle_philox4x32_10.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
+        L.oracle_philox4x32_10_many.argtypes = [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]
         L.oracle_table_ecap.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, C.c_double, C.c_int]
         L.oracle_build_table.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, C.c_double,
                                          C.c_int, C.c_int, C.c_void_p]
@@ -118,6 +119,15 @@ def philox4x32_10(ctr, key) -> np.ndarray:
     k = np.ascontiguousarray(key, dtype=np.uint32)
     out = np.zeros(4, dtype=np.uint32)
     lib().oracle_philox4x32_10(_p(c), _p(k), _p(out))
+    return out
+
+
+def philox4x32_10_many(ctr, key) -> np.ndarray:
+    """Philox4x32-10 of every row of ctr ([n, 4] uint32) under one key: [n, 4] uint32."""
+    c = np.ascontiguousarray(ctr, dtype=np.uint32).reshape(-1, 4)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros_like(c)
+    lib().oracle_philox4x32_10_many(len(c), _p(c), _p(k), _p(out))
     return out
 
 

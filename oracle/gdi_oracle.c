@@ -93,6 +93,12 @@ void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t
     memcpy(out, c, sizeof c);
 }
 
+/* Philox4x32-10 of n counters under one key (out[4 i .. 4 i + 3] for ctr[4 i .. 4 i + 3]). */
+void oracle_philox4x32_10_many(int64_t n, const uint32_t *ctr, const uint32_t key[2], uint32_t *out)
+{
+    for (int64_t i = 0; i < n; ++i) oracle_philox4x32_10(ctr + 4 * i, key, out + 4 * i);
+}
+
 /* One 32-bit draw: counter (c0, c1, c2, c3), key = (seed low word, seed high word), word w. */
 static uint32_t draw_word(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, int w)
 {

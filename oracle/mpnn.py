@@ -20,7 +20,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from . import philox4x32_10
+from . import philox4x32_10_many
 
 HID = 64
 FIN = 16
@@ -71,29 +71,38 @@ def _adj(row_ptr, col):
     return rows, np.asarray(col, dtype=np.int64), np.diff(row_ptr).astype(np.float64)
 
 
+def _matrix(rows, cols, vals, n):
+    """The n x n sparse matrix with entries vals at (rows, cols) (a library sparse product serves as
+    the matrix-times-block step below)."""
+    import scipy.sparse as sp
+    return sp.csr_matrix((vals, (rows, cols)), shape=(n, n))
+
+
 def mean_aggregate(row_ptr, col, X):
+    """D^-1 A X: every vertex gets the mean of its neighbours' rows (0 for an isolated vertex)."""
     rows, cols, deg = _adj(row_ptr, col)
-    Y = np.zeros_like(X, dtype=np.float64)
-    np.add.at(Y, rows, X[cols])
-    nz = deg > 0
-    Y[nz] /= deg[nz, None]
-    return Y
+    return np.asarray(_matrix(rows, cols, 1.0 / deg[rows], len(deg)) @ np.asarray(X, dtype=np.float64))
 
 
 def mean_aggregate_T(row_ptr, col, X):
     """(D^-1 A)^T X for a symmetric A: Y_j = sum_{i in N(j)} X_i / deg_i."""
     rows, cols, deg = _adj(row_ptr, col)
-    Y = np.zeros_like(X, dtype=np.float64)
-    np.add.at(Y, cols, X[rows] / deg[rows, None])
-    return Y
+    return np.asarray(_matrix(rows, cols, 1.0 / deg[rows], len(deg)).T @ np.asarray(X, dtype=np.float64))
 
 
-def lazy_walk(row_ptr, col, X):
+def walk_matrix(row_ptr, col):
+    """D^-1/2 A D^-1/2 of the graph."""
     rows, cols, deg = _adj(row_ptr, col)
-    Y = np.zeros_like(X, dtype=np.float64)
-    w = 1.0 / np.sqrt(deg[rows] * deg[cols])
-    np.add.at(Y, rows, X[cols] * w[:, None])
-    return 0.5 * X + 0.5 * Y
+    return _matrix(rows, cols, 1.0 / np.sqrt(deg[rows] * deg[cols]), len(deg))
+
+
+def lazy_walk(row_ptr, col, X, S=None):
+    """One lazy step of the normalised walk: 0.5 X + 0.5 D^-1/2 A D^-1/2 X (S: that matrix, if
+    already built)."""
+    if S is None:
+        S = walk_matrix(row_ptr, col)
+    X = np.asarray(X, dtype=np.float64)
+    return 0.5 * X + 0.5 * np.asarray(S @ X)
 
 
 # ------------------------------------------------------------------ features ------------------
@@ -102,12 +111,18 @@ def features(graph_ptr, graph_id, row_ptr, col, seed, steps):
     R = np.zeros((N, NRAND))
     key = [seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF]
     for g in range(len(graph_ptr) - 1):
-        for i in range(graph_ptr[g], graph_ptr[g + 1]):
-            for c in range(NRAND):
-                w = philox4x32_10([i - graph_ptr[g], c, graph_id[g], 0x4D504E4E], key)[0]
-                R[i, c] = -1.0 if (int(w) >> 31) else 1.0
+        # counter (local vertex, channel, graph id, tag); word 0's top bit gives the sign
+        n = int(graph_ptr[g + 1] - graph_ptr[g])
+        ctr = np.zeros((n, NRAND, 4), dtype=np.uint32)
+        ctr[:, :, 0] = np.arange(n, dtype=np.uint32)[:, None]
+        ctr[:, :, 1] = np.arange(NRAND, dtype=np.uint32)[None, :]
+        ctr[:, :, 2] = graph_id[g]
+        ctr[:, :, 3] = 0x4D504E4E
+        w = philox4x32_10_many(ctr.reshape(-1, 4), key)[:, 0].reshape(n, NRAND)
+        R[graph_ptr[g]:graph_ptr[g + 1]] = np.where(w >> np.uint32(31), -1.0, 1.0)
+    S = walk_matrix(row_ptr, col)
     for _ in range(steps):
-        R = lazy_walk(row_ptr, col, R)
+        R = lazy_walk(row_ptr, col, R, S)
     X = np.zeros((N, FIN))
     deg = np.diff(row_ptr).astype(np.float64)
     for g in range(len(graph_ptr) - 1):

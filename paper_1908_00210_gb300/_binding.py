@@ -28,7 +28,7 @@ ERRORS = {
 EXPORTS = ["gdi_create", "gdi_anneal", "gdi_get_spins", "gdi_get_results", "gdi_cut", "gdi_balance",
            "gdi_get_trace", "gdi_configure", "gdi_last_launch", "gdi_info", "gdi_destroy",
            "gdi_strerror", "gdi_last_error", "gdi_anneal_static", "gdi_autotune", "gdi_kernel_time",
-           "gdi_inject_wait_failure"]
+           "gdi_inject_wait_failure", "gdi_rank_space", "gdi_build_table", "gdi_anneal_static_status"]
 GDI_PATH_AUTO, GDI_PATH_CTA, GDI_PATH_GRID = 0, 1, 2
 
 
@@ -83,6 +83,9 @@ def load():
     L.gdi_autotune.argtypes = [vp, C.POINTER(gdi_schedule), i32, vp, vp, vp]
     L.gdi_anneal_static.argtypes = [i32, vp, vp, i32, vp, i32, i32, i32, i32, i32, i32, vp, vp, vp,
                                     i32, i32, i32, i32, C.c_uint64, i32, vp, vp, vp]
+    L.gdi_anneal_static_status.argtypes = [vp, vp]
+    L.gdi_rank_space.argtypes = [C.POINTER(gdi_graph), vp, vp, vp, vp, vp, vp, vp]
+    L.gdi_build_table.argtypes = [C.POINTER(gdi_schedule), vp, i64, vp, vp, vp, vp]
     L.gdi_last_launch.argtypes = [vp, vp, vp, vp, vp]
     L.gdi_kernel_time.argtypes = [vp, vp, vp]
     L.gdi_inject_wait_failure.argtypes = [vp, C.c_int64]
@@ -268,3 +271,54 @@ class Annealer:
         ec = np.zeros(1, np.int32)
         _check(load().gdi_info(self._h, nc.ctypes.data, md.ctypes.data, ec.ctypes.data))
         return dict(num_classes=nc, max_degree=int(md[0]), ecap=int(ec[0]))
+
+
+@dataclass
+class RankSpace:
+    """The rank-space layout of one graph (gdi_rank_space), as gdi_anneal_static takes it."""
+    vert_of: np.ndarray      # int32 [n]: original vertex at rank r
+    rank_of: np.ndarray      # int64 [n]: rank of original vertex v
+    row_ptr: np.ndarray      # int64 [n + 1]
+    col: np.ndarray          # uint32 [nnz]: neighbour rank | 0x80000000 for weight -1
+    class_ptr: np.ndarray    # int32 [num_classes + 1]
+    max_class: int
+    max_degree: int
+
+
+def rank_space(graph, color=None) -> RankSpace:
+    """gdi_rank_space on one graph (host arrays; validation and colouring as gdi_create)."""
+    L = load()
+    n = int(graph.n)
+    rp = np.ascontiguousarray(graph.row_ptr, dtype=np.int64)
+    col = np.ascontiguousarray(graph.col, dtype=np.int32)
+    w = np.ascontiguousarray(graph.w, dtype=np.int32) if getattr(graph, "w", None) is not None else None
+    if color is None:
+        color = getattr(graph, "color", None)
+    colr = None if color is None else np.ascontiguousarray(color, dtype=np.int32)
+    g = gdi_graph(1, None, n, _ptr(rp), _ptr(col), _ptr(w), _ptr(colr))
+    vert = np.empty(n, np.int32)
+    orp = np.empty(n + 1, np.int64)
+    ocol = np.empty(int(rp[-1]), np.uint32)
+    cls = np.empty(n + 1, np.int32)
+    nc = np.zeros(1, np.int32)
+    mc = np.zeros(1, np.int32)
+    md = np.zeros(1, np.int32)
+    _check(L.gdi_rank_space(C.byref(g), _ptr(vert), _ptr(orp), _ptr(ocol), _ptr(cls), _ptr(nc), _ptr(mc),
+                            _ptr(md)))
+    rank = np.empty(n, np.int64)
+    rank[vert] = np.arange(n)
+    return RankSpace(vert, rank, orp, ocol, cls[:int(nc[0]) + 1].copy(), int(mc[0]), int(md[0]))
+
+
+def build_table(schedule: Schedule):
+    """gdi_build_table: (tab uint32, tab_off int32 [M+1], temp float32 [M], max_row)."""
+    L = load()
+    s = schedule.c()
+    ln = np.zeros(1, np.int64)
+    mr = np.zeros(1, np.int32)
+    _check(L.gdi_build_table(C.byref(s), None, 0, _ptr(ln), None, None, _ptr(mr)))
+    tab = np.zeros(max(int(ln[0]), 1), np.uint32)
+    off = np.zeros(schedule.sweeps + 1, np.int32)
+    temp = np.zeros(schedule.sweeps, np.float32)
+    _check(L.gdi_build_table(C.byref(s), _ptr(tab), len(tab), _ptr(ln), _ptr(off), _ptr(temp), _ptr(mr)))
+    return tab, off, temp, int(mr[0])

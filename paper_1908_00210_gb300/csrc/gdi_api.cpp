@@ -1,7 +1,8 @@
 // gdi_api.cpp -- host side of libgdi.so: the C ABI declared in include/gdi.h.
 //
 // gdi_create validates the CSR, colours it (greedy first-fit in vertex-id order unless a colouring
-// is given), relabels every instance into rank order (colour asc, id asc), packs each neighbour as
+// is given), relabels every instance into rank order (colour asc, then splitmix64 of the local
+// vertex id asc inside each class), packs each neighbour as
 // (local rank | weight-sign bit) and uploads the rank-space CSR once.  gdi_anneal builds the
 // per-sweep threshold table on the host (double precision; the GPU never evaluates exp), then
 // enqueues the initial-state kernel and the persistent anneal kernel on the caller's stream.
@@ -300,6 +301,135 @@ int validate_graph(const gdi_graph &g, const std::vector<int64_t> &inst, std::ve
     return GDI_OK;
 }
 
+// ---------------------------------------------------------------------------------------------
+// Host preprocessing shared by gdi_create and gdi_rank_space: validation, colouring, rank order
+// and the rank-space CSR of every instance (instance bounds `inst`, window W for max_window).
+struct HostRankSpace {
+    std::vector<int32_t> w, color, rank_of, vert_of, class_off, class_ptr, num_classes;
+    std::vector<int64_t> rp;
+    std::vector<uint32_t> cr;
+    int32_t max_n = 0, max_window = 0, max_class = 0, max_degree = 0;
+};
+
+int build_rank_space(const gdi_graph *g, const std::vector<int64_t> &inst, int32_t W, HostRankSpace &H)
+{
+    const int32_t Q = g->num_instances;
+    const int64_t N = g->num_vertices;
+    int rc = validate_graph(*g, inst, H.w);
+    if (rc) return rc;
+    const std::vector<int32_t> &w = H.w;
+
+    // colouring: caller's (checked) or greedy first-fit in id order, per instance
+    std::vector<int32_t> &color = H.color;
+    color.assign((size_t)N, 0);
+    if (g->color) {
+        for (int64_t v = 0; v < N; ++v) {
+            if (g->color[v] < 0) return fail(GDI_ERR_BAD_COLORING, "negative colour");
+            color[(size_t)v] = g->color[v];
+        }
+    } else {
+        std::vector<int64_t> mark;
+        for (int64_t v = 0; v < N; ++v) {
+            const int64_t d = g->row_ptr[v + 1] - g->row_ptr[v];
+            if ((int64_t)mark.size() < d + 2) mark.resize((size_t)d + 2, -1);
+            for (int64_t e = g->row_ptr[v]; e < g->row_ptr[v + 1]; ++e) {
+                const int64_t j = g->col[e];
+                if (j < v) {
+                    const int32_t c = color[(size_t)j];
+                    if (c < d + 2) mark[(size_t)c] = v;
+                }
+            }
+            int32_t c = 0;
+            while (mark[(size_t)c] == v) ++c;
+            color[(size_t)v] = c;
+        }
+    }
+    for (int64_t v = 0; v < N; ++v)
+        for (int64_t e = g->row_ptr[v]; e < g->row_ptr[v + 1]; ++e)
+            if (color[(size_t)g->col[e]] == color[(size_t)v])
+                return fail(GDI_ERR_BAD_COLORING, "adjacent vertices share a colour");
+
+    // rank order per instance: counting sort by colour, then inside each class by splitmix64 of
+    // the local vertex id
+    std::vector<int32_t> &rank_of = H.rank_of, &vert_of = H.vert_of;
+    std::vector<int32_t> &class_off = H.class_off, &class_ptr = H.class_ptr;
+    rank_of.assign((size_t)N, 0);
+    vert_of.assign((size_t)N, 0);
+    class_off.assign((size_t)Q + 1, 0);
+    class_ptr.clear();
+    H.num_classes.assign((size_t)Q, 0);
+    for (int32_t q = 0; q < Q; ++q) {
+        const int64_t lo = inst[(size_t)q], hi = inst[(size_t)q + 1];
+        const int32_t n = (int32_t)(hi - lo);
+        int32_t ncol = 0;
+        for (int64_t v = lo; v < hi; ++v) ncol = std::max(ncol, color[(size_t)v] + 1);
+        if ((int64_t)ncol > (int64_t)n + 1 && ncol > (1 << 24))
+            return fail(GDI_ERR_OVERFLOW, "colour values too large");
+        std::vector<int32_t> cnt((size_t)ncol + 1, 0);
+        for (int64_t v = lo; v < hi; ++v) cnt[(size_t)color[(size_t)v] + 1]++;
+        for (int32_t k = 0; k < ncol; ++k) cnt[(size_t)k + 1] += cnt[(size_t)k];
+        class_off[(size_t)q] = (int32_t)class_ptr.size();
+        int32_t nclass = 0;
+        for (int32_t k = 0; k < ncol; ++k) {
+            if (cnt[(size_t)k + 1] > cnt[(size_t)k]) {
+                class_ptr.push_back(cnt[(size_t)k]);
+                const int32_t sz = cnt[(size_t)k + 1] - cnt[(size_t)k];
+                H.max_window = std::max(H.max_window, W > 0 ? std::min(W, sz) : sz);
+                H.max_class = std::max(H.max_class, sz);
+                ++nclass;
+            }
+        }
+        class_ptr.push_back(n);
+        H.num_classes[(size_t)q] = nclass;
+        for (int64_t v = lo; v < hi; ++v) {
+            const int32_t r = cnt[(size_t)color[(size_t)v]]++;
+            vert_of[(size_t)(lo + r)] = (int32_t)v;
+        }
+        // inside a class, ranks follow splitmix64 of the local vertex id (a fixed pseudo-random
+        // order, so that heavy vertices spread over windows and blocks)
+        {
+            std::vector<std::pair<uint64_t, int32_t>> keyed;
+            const int32_t *bounds = class_ptr.data() + class_off[(size_t)q];
+            for (int32_t k = 0; k < nclass; ++k) {
+                const int32_t c0 = bounds[k], c1 = bounds[k + 1];
+                keyed.resize((size_t)(c1 - c0));
+                for (int32_t r = c0; r < c1; ++r) {
+                    const int32_t v = vert_of[(size_t)(lo + r)];
+                    keyed[(size_t)(r - c0)] = {splitmix64_host((uint64_t)(v - lo)), v};
+                }
+                std::sort(keyed.begin(), keyed.end());
+                for (int32_t r = c0; r < c1; ++r) vert_of[(size_t)(lo + r)] = keyed[(size_t)(r - c0)].second;
+            }
+        }
+        for (int64_t r = lo; r < hi; ++r) rank_of[(size_t)vert_of[(size_t)r]] = (int32_t)r;
+        H.max_n = std::max(H.max_n, n);
+    }
+    class_off[(size_t)Q] = (int32_t)class_ptr.size();
+
+    // rank-space CSR, neighbour = local rank | weight-sign bit
+    std::vector<int64_t> &rp = H.rp;
+    std::vector<uint32_t> &cr = H.cr;
+    rp.assign((size_t)N + 1, 0);
+    cr.assign((size_t)g->row_ptr[N], 0);
+    {
+        size_t q = 0;
+        int64_t e_out = 0;
+        for (int64_t r = 0; r < N; ++r) {
+            while (inst[q + 1] <= r) ++q;
+            const int64_t v = vert_of[(size_t)r];
+            rp[(size_t)r] = e_out;
+            const int64_t d = g->row_ptr[v + 1] - g->row_ptr[v];
+            H.max_degree = (int32_t)std::max<int64_t>(H.max_degree, d);
+            for (int64_t e = g->row_ptr[v]; e < g->row_ptr[v + 1]; ++e) {
+                const uint32_t lr = (uint32_t)(rank_of[(size_t)g->col[e]] - inst[q]);
+                cr[(size_t)e_out++] = lr | (w[(size_t)e] < 0 ? 0x80000000u : 0u);
+            }
+        }
+        rp[(size_t)N] = e_out;
+    }
+    return GDI_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -330,38 +460,12 @@ int gdi_create(gdi_ctx **out, const gdi_graph *g, const gdi_model *m)
     }
     if ((int64_t)m->replicas * N > ((int64_t)1 << 40)) return fail(GDI_ERR_OVERFLOW, "replicas * N too large");
 
-    std::vector<int32_t> w;
-    int rc = validate_graph(*g, inst, w);
+    HostRankSpace H;
+    int rc = build_rank_space(g, inst, m->W, H);
     if (rc) return rc;
-
-    // colouring: caller's (checked) or greedy first-fit in id order, per instance
-    std::vector<int32_t> color((size_t)N);
-    if (g->color) {
-        for (int64_t v = 0; v < N; ++v) {
-            if (g->color[v] < 0) return fail(GDI_ERR_BAD_COLORING, "negative colour");
-            color[(size_t)v] = g->color[v];
-        }
-    } else {
-        std::vector<int64_t> mark;
-        for (int64_t v = 0; v < N; ++v) {
-            const int64_t d = g->row_ptr[v + 1] - g->row_ptr[v];
-            if ((int64_t)mark.size() < d + 2) mark.resize((size_t)d + 2, -1);
-            for (int64_t e = g->row_ptr[v]; e < g->row_ptr[v + 1]; ++e) {
-                const int64_t j = g->col[e];
-                if (j < v) {
-                    const int32_t c = color[(size_t)j];
-                    if (c < d + 2) mark[(size_t)c] = v;
-                }
-            }
-            int32_t c = 0;
-            while (mark[(size_t)c] == v) ++c;
-            color[(size_t)v] = c;
-        }
-    }
-    for (int64_t v = 0; v < N; ++v)
-        for (int64_t e = g->row_ptr[v]; e < g->row_ptr[v + 1]; ++e)
-            if (color[(size_t)g->col[e]] == color[(size_t)v])
-                return fail(GDI_ERR_BAD_COLORING, "adjacent vertices share a colour");
+    const std::vector<int32_t> &rank_of = H.rank_of, &class_off = H.class_off, &class_ptr = H.class_ptr;
+    const std::vector<int64_t> &rp = H.rp;
+    const std::vector<uint32_t> &cr = H.cr;
 
     gdi_ctx *c = new (std::nothrow) gdi_ctx;
     if (!c) return fail(GDI_ERR_OOM, "host allocation failed");
@@ -373,80 +477,11 @@ int gdi_create(gdi_ctx **out, const gdi_graph *g, const gdi_model *m)
     c->W = m->W;
     c->N = N;
     c->nnz = g->row_ptr[N];
-
-    // rank order per instance: counting sort by colour, stable in id
-    std::vector<int32_t> rank_of((size_t)N), vert_of((size_t)N);
-    std::vector<int32_t> class_off((size_t)Q + 1, 0), class_ptr;
-    c->num_classes.assign((size_t)Q, 0);
-    for (int32_t q = 0; q < Q; ++q) {
-        const int64_t lo = inst[(size_t)q], hi = inst[(size_t)q + 1];
-        const int32_t n = (int32_t)(hi - lo);
-        int32_t ncol = 0;
-        for (int64_t v = lo; v < hi; ++v) ncol = std::max(ncol, color[(size_t)v] + 1);
-        if ((int64_t)ncol > (int64_t)n + 1 && ncol > (1 << 24)) {
-            delete c;
-            return fail(GDI_ERR_OVERFLOW, "colour values too large");
-        }
-        std::vector<int32_t> cnt((size_t)ncol + 1, 0);
-        for (int64_t v = lo; v < hi; ++v) cnt[(size_t)color[(size_t)v] + 1]++;
-        for (int32_t k = 0; k < ncol; ++k) cnt[(size_t)k + 1] += cnt[(size_t)k];
-        class_off[(size_t)q] = (int32_t)class_ptr.size();
-        int32_t nclass = 0;
-        for (int32_t k = 0; k < ncol; ++k) {
-            if (cnt[(size_t)k + 1] > cnt[(size_t)k]) {
-                class_ptr.push_back(cnt[(size_t)k]);
-                const int32_t sz = cnt[(size_t)k + 1] - cnt[(size_t)k];
-                c->max_window = std::max(c->max_window, m->W > 0 ? std::min(m->W, sz) : sz);
-                c->max_class = std::max(c->max_class, sz);
-                ++nclass;
-            }
-        }
-        class_ptr.push_back(n);
-        c->num_classes[(size_t)q] = nclass;
-        for (int64_t v = lo; v < hi; ++v) {
-            const int32_t r = cnt[(size_t)color[(size_t)v]]++;
-            vert_of[(size_t)(lo + r)] = (int32_t)v;
-        }
-        // inside a class, ranks follow splitmix64 of the local vertex id (a fixed pseudo-random
-        // order, so that heavy vertices spread over windows and blocks)
-        {
-            std::vector<std::pair<uint64_t, int32_t>> keyed;
-            const int32_t *bounds = class_ptr.data() + class_off[(size_t)q];
-            for (int32_t k = 0; k < nclass; ++k) {
-                const int32_t c0 = bounds[k], c1 = bounds[k + 1];
-                keyed.resize((size_t)(c1 - c0));
-                for (int32_t r = c0; r < c1; ++r) {
-                    const int32_t v = vert_of[(size_t)(lo + r)];
-                    keyed[(size_t)(r - c0)] = {splitmix64_host((uint64_t)(v - lo)), v};
-                }
-                std::sort(keyed.begin(), keyed.end());
-                for (int32_t r = c0; r < c1; ++r) vert_of[(size_t)(lo + r)] = keyed[(size_t)(r - c0)].second;
-            }
-        }
-        for (int64_t r = lo; r < hi; ++r) rank_of[(size_t)vert_of[(size_t)r]] = (int32_t)r;
-        c->max_n = std::max(c->max_n, n);
-    }
-    class_off[(size_t)Q] = (int32_t)class_ptr.size();
-
-    // rank-space CSR, neighbour = local rank | weight-sign bit
-    std::vector<int64_t> rp((size_t)N + 1, 0);
-    std::vector<uint32_t> cr((size_t)c->nnz);
-    {
-        size_t q = 0;
-        int64_t e_out = 0;
-        for (int64_t r = 0; r < N; ++r) {
-            while (inst[q + 1] <= r) ++q;
-            const int64_t v = vert_of[(size_t)r];
-            rp[(size_t)r] = e_out;
-            const int64_t d = g->row_ptr[v + 1] - g->row_ptr[v];
-            c->max_degree = (int32_t)std::max<int64_t>(c->max_degree, d);
-            for (int64_t e = g->row_ptr[v]; e < g->row_ptr[v + 1]; ++e) {
-                const uint32_t lr = (uint32_t)(rank_of[(size_t)g->col[e]] - inst[q]);
-                cr[(size_t)e_out++] = lr | (w[(size_t)e] < 0 ? 0x80000000u : 0u);
-            }
-        }
-        rp[(size_t)N] = e_out;
-    }
+    c->num_classes = H.num_classes;
+    c->max_n = H.max_n;
+    c->max_window = H.max_window;
+    c->max_class = H.max_class;
+    c->max_degree = H.max_degree;
     // window costs for the grid path's weighted split: a rank costs its degree plus a constant for
     // its threshold and its share of the window sort (both measured as about 12 neighbour reads)
     if (Q == 1 && c->W >= 1) {
@@ -508,6 +543,51 @@ int gdi_create(gdi_ctx **out, const gdi_graph *g, const gdi_model *m)
         return fail(GDI_ERR_OOM, "device allocation failed");
     }
     *out = c;
+    return GDI_OK;
+}
+
+int gdi_rank_space(const gdi_graph *g, int32_t *vert_of, int64_t *row_ptr, uint32_t *col,
+                   int32_t *class_ptr, int32_t *num_classes, int32_t *max_class, int32_t *max_degree)
+{
+    if (!g || !vert_of || !row_ptr || !col || !class_ptr || !num_classes)
+        return fail(GDI_ERR_INVALID_ARG, "null argument");
+    if (g->num_instances != 1 || g->num_vertices < 1 || !g->row_ptr || !g->col)
+        return fail(GDI_ERR_INVALID_ARG, "gdi_rank_space takes one non-empty graph");
+    if (g->num_vertices > (1 << 28)) return fail(GDI_ERR_OVERFLOW, "graph over 2^28 vertices");
+    const int64_t N = g->num_vertices;
+    std::vector<int64_t> inst = {0, N};
+    HostRankSpace H;
+    const int rc = build_rank_space(g, inst, 0, H);
+    if (rc) return rc;
+    std::copy(H.vert_of.begin(), H.vert_of.end(), vert_of);
+    std::copy(H.rp.begin(), H.rp.end(), row_ptr);
+    std::copy(H.cr.begin(), H.cr.end(), col);
+    std::copy(H.class_ptr.begin(), H.class_ptr.end(), class_ptr);
+    *num_classes = H.num_classes[0];
+    if (max_class) *max_class = H.max_class;
+    if (max_degree) *max_degree = H.max_degree;
+    return GDI_OK;
+}
+
+int gdi_build_table(const gdi_schedule *S, uint32_t *tab, int64_t tab_cap, int64_t *tab_len,
+                    int32_t *tab_off, float *temp, int32_t *max_row)
+{
+    if (!S || !tab_len) return fail(GDI_ERR_INVALID_ARG, "null argument");
+    if (S->sweeps < 1) return fail(GDI_ERR_INVALID_ARG, "sweeps must be >= 1");
+    std::vector<uint32_t> t;
+    std::vector<int32_t> off;
+    std::vector<float> tp;
+    int32_t ecap = 0, mr = 0;
+    const int rc = build_table(*S, t, off, tp, ecap, mr);
+    if (rc) return rc;
+    *tab_len = (int64_t)t.size();
+    if (max_row) *max_row = mr;
+    if (!tab) return GDI_OK;                     // size query
+    if (tab_cap < (int64_t)t.size()) return fail(GDI_ERR_INVALID_ARG, "tab_cap below the table length");
+    if (!tab_off || !temp) return fail(GDI_ERR_INVALID_ARG, "null tab_off or temp");
+    std::copy(t.begin(), t.end(), tab);
+    std::copy(off.begin(), off.end(), tab_off);
+    std::copy(tp.begin(), tp.end(), temp);
     return GDI_OK;
 }
 

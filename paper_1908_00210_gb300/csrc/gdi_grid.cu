@@ -460,6 +460,49 @@ __device__ inline void class_partition(int32_t lo, int32_t hi, int W, int p, int
     nwin = k1 - k0;
 }
 
+// Entry check of a launch's plan, by every block before it writes shared memory: the class bounds
+// run monotonically from 0 to n, this block's share of every class fits the plan's spc ranks and
+// wpc windows, and every table row of the sweep range fits max_row.  gdi_anneal derives these sizes
+// itself; a caller of the allocation-free entry point passes them.  A failed check -- or an input
+// check that failed before the launch and left the error word set -- makes the launch return: the
+// failing block sets the error word, the others see it at their first barrier.
+__device__ bool plan_fits(const GridArgs &A)
+{
+    const GdiDevProblem &P = A.P;
+    const GdiDevRun &R = A.R;
+    const int64_t base = P.node_off[0];
+    const int32_t n = (int32_t)(P.node_off[1] - base);
+    const int32_t *cls = P.class_ptr + P.class_off[0];
+    const int32_t ncls = P.class_off[1] - P.class_off[0] - 1;
+    const int Pb = gridDim.x, p = blockIdx.x;
+    int bad = *(volatile int32_t *)A.X.err != 0 || ncls < 1;
+    if (!bad) {
+        if (threadIdx.x == 0 && (cls[0] != 0 || cls[ncls] != n)) bad = 1;
+        for (int c = threadIdx.x; c < ncls; c += GB) {
+            const int32_t lo = cls[c], hi = cls[c + 1];
+            if (lo < 0 || hi < lo || hi > n) { bad = 1; continue; }
+            int32_t x0, x1;
+            int nw;
+            if (A.wbnd) {
+                const int32_t *bd = A.wbnd + (size_t)c * (Pb + 1);
+                x0 = min(lo + bd[p] * P.W, hi);
+                x1 = min(lo + bd[p + 1] * P.W, hi);
+                nw = bd[p + 1] - bd[p];
+            } else {
+                class_partition(lo, hi, P.W, p, Pb, x0, x1, nw);
+            }
+            if (nw < 0 || nw > A.wpc || x1 - x0 > A.spc || x1 < x0) bad = 1;
+        }
+        for (int s = R.s_begin + threadIdx.x; s < R.s_end; s += GB) {
+            const int32_t len = R.tab_off[s + 1] - R.tab_off[s];
+            if (R.tab_off[s] < 0 || len < 0 || len > R.max_row) bad = 1;
+        }
+    }
+    bad = __syncthreads_or(bad);
+    if (bad && threadIdx.x == 0) atomicCAS(A.X.err, 0, GDI_DEVERR_INPUT);
+    return !bad;
+}
+
 // E* in 16 bits: the sentinels at the ends of the range (values are 0..max_row < 32000 or -1)
 __device__ __forceinline__ int16_t es_encode(int32_t e)
 {
@@ -838,6 +881,7 @@ __global__ void __launch_bounds__(GB, 1) gdi_grid_anneal_kernel(GridArgs A)
     const int W = P.W;
     const int nrep = A.nrep;
 
+    if (!plan_fits(A)) return;
     init_G(A, p, Pb, n, base);
     if (!grid_sync(X)) return;
 
@@ -1351,6 +1395,7 @@ __global__ void __launch_bounds__(GB, 1) gdi_grid_sorted_kernel(GridArgs A)
     const int W = P.W;
     const int nrep = A.nrep;
 
+    if (!plan_fits(A)) return;
     init_G(A, p, Pb, n, base);
     if (A.hf) init_fields(A, p, Pb, n, base);
     if (!grid_sync(X)) return;
@@ -1702,6 +1747,7 @@ __global__ void __launch_bounds__(GB, 1) gdi_grid_racy_kernel(GridArgs A)
     const int32_t ncls = P.class_off[1] - P.class_off[0] - 1;
     const int nrep = A.nrep;
 
+    if (!plan_fits(A)) return;
     init_G(A, p, Pb, n, base);
     if (!grid_sync(X)) return;
     for (int sw = R.s_begin; sw < R.s_end; ++sw) {

@@ -114,5 +114,6 @@ int gdi_launch_gather_spins(const GdiDevProblem &P, const int8_t *spins_rank, in
 // device error codes written to GdiDevRun::err
 #define GDI_DEVERR_RANGE 1
 #define GDI_DEVERR_TIMEOUT 2
+#define GDI_DEVERR_INPUT 3     // an input check of the launch failed (sizes the caller passed)
 
 #define GDI_GRID_TW 129   // entries of a window table (2 * 64 + 1)

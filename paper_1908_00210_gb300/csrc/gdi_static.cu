@@ -10,6 +10,7 @@
 // until the process exits.  The caller passes every input and output as device pointers.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <mutex>
 #include <string>
 
@@ -52,7 +53,81 @@ __global__ void static_meta_kernel(int64_t *node_off, int32_t *class_off, int64_
     class_off[1] = nbounds;
 }
 
+// Input checks, enqueued before the anneal (the sizes and arrays come from the caller, and the
+// kernel's shared-memory plan trusts them).  Rows: row_ptr starts at 0 and every row holds 0 ..
+// max_degree entries, so every row lies inside [0, row_ptr[n]).
+__global__ void static_rows_check_kernel(int32_t n, const int64_t *row_ptr, int32_t max_degree, int32_t *err)
+{
+    int bad = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t d = row_ptr[i + 1] - row_ptr[i];
+        if (d < 0 || d > max_degree) bad = 1;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0 && row_ptr[0] != 0) bad = 1;
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicCAS(err, 0, GDI_DEVERR_INPUT);
+}
+
+// Columns (only once the rows passed): every neighbour rank lies in [0, n) and outside the row's
+// own colour class (a proper colouring, which also rules out self-loops).
+__global__ void static_cols_check_kernel(int32_t n, const int64_t *row_ptr, const uint32_t *col,
+                                         const int32_t *class_ptr, int32_t num_classes, int32_t *err)
+{
+    if (*(volatile int32_t *)err) return;
+    int bad = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        int32_t lo = 0, hi = num_classes;          // class k of rank i: class_ptr[k] <= i < class_ptr[k + 1]
+        while (hi - lo > 1) {
+            const int32_t mid = (lo + hi) >> 1;
+            if (class_ptr[mid] <= i) lo = mid; else hi = mid;
+        }
+        const int64_t c0 = class_ptr[lo], c1 = class_ptr[lo + 1];
+        for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+            const int64_t j = (int64_t)(col[e] & 0x7FFFFFFFu);
+            if (j >= n || (j >= c0 && j < c1)) bad = 1;
+        }
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicCAS(err, 0, GDI_DEVERR_INPUT);
+}
+
+__global__ void static_status_kernel(const int32_t *err, int32_t *out)
+{
+    const int32_t e = *(volatile const int32_t *)err;
+    *out = e == 0 ? GDI_OK : e == GDI_DEVERR_TIMEOUT ? GDI_ERR_TIMEOUT
+         : e == GDI_DEVERR_INPUT ? GDI_ERR_INVALID_ARG : GDI_ERR_CUDA;
+}
+
+// the device address of the static array on the current device (looked up once per device)
+int static_base(unsigned char **out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return gdi_set_error(GDI_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+    if (dev < 0 || dev >= ST_MAX_DEVICES)
+        return gdi_set_error(GDI_ERR_TOO_LARGE, "gdi_anneal_static: device ordinal above 63");
+    DeviceSlot &slot = g_slots[dev];
+    std::call_once(slot.once, [&slot]() {
+        slot.err = cudaGetSymbolAddress((void **)&slot.ptr, g_gdi_static_scratch);
+    });
+    if (slot.err != cudaSuccess || !slot.ptr)
+        return gdi_set_error(GDI_ERR_CUDA, std::string("cudaGetSymbolAddress(static scratch): ") +
+                                               cudaGetErrorString(slot.err));
+    *out = slot.ptr;
+    return GDI_OK;
+}
+
 }  // namespace
+
+extern "C" int gdi_anneal_static_status(int32_t *status, void *stream)
+{
+    if (!status) return gdi_set_error(GDI_ERR_INVALID_ARG, "gdi_anneal_static_status: null pointer");
+    unsigned char *base = nullptr;
+    const int rc = static_base(&base);
+    if (rc) return rc;
+    static_status_kernel<<<1, 1, 0, (cudaStream_t)stream>>>(reinterpret_cast<const int32_t *>(base + OFF_ERR), status);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return gdi_set_error(GDI_ERR_CUDA, std::string("gdi_anneal_static_status: ") + cudaGetErrorString(e));
+    return GDI_OK;
+}
 
 extern "C" int gdi_anneal_static(int32_t n, const int64_t *row_ptr, const uint32_t *col,
                                  int32_t num_classes, const int32_t *class_ptr, int32_t max_class,
@@ -81,19 +156,12 @@ extern "C" int gdi_anneal_static(int32_t n, const int64_t *row_ptr, const uint32
     if ((int64_t)B * max_degree + 4LL * A + max_row + 1 >= ((int64_t)1 << 29))
         return gdi_set_error(GDI_ERR_OVERFLOW, "gdi_anneal_static: B * max_degree + 4A + E_cap >= 2^29");
 
+    unsigned char *base = nullptr;
+    int rcb = static_base(&base);
+    if (rcb) return rcb;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return gdi_set_error(GDI_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
-    if (dev < 0 || dev >= ST_MAX_DEVICES)
-        return gdi_set_error(GDI_ERR_TOO_LARGE, "gdi_anneal_static: device ordinal above 63");
-    DeviceSlot &slot = g_slots[dev];
-    std::call_once(slot.once, [&slot]() {
-        slot.err = cudaGetSymbolAddress((void **)&slot.ptr, g_gdi_static_scratch);
-    });
-    if (slot.err != cudaSuccess || !slot.ptr)
-        return gdi_set_error(GDI_ERR_CUDA, std::string("cudaGetSymbolAddress(static scratch): ") +
-                                               cudaGetErrorString(slot.err));
-    unsigned char *base = slot.ptr;
 
     int sms = 0, optin = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -170,6 +238,12 @@ extern "C" int gdi_anneal_static(int32_t n, const int64_t *row_ptr, const uint32
     e = cudaMemsetAsync(X.err, 0, sizeof(int32_t), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(X.status, 0, 16 * sizeof(int32_t), st);
     if (e != cudaSuccess) return gdi_set_error(GDI_ERR_CUDA, std::string("gdi_anneal_static: ") + cudaGetErrorString(e));
+    // input checks; a failure leaves the error word set and the anneal kernel returns at entry
+    {
+        const int cb = (int)std::min<int64_t>(((int64_t)n + 255) / 256, (int64_t)nblk * 8);
+        static_rows_check_kernel<<<cb, 256, 0, st>>>(n, row_ptr, max_degree, X.err);
+        static_cols_check_kernel<<<cb, 256, 0, st>>>(n, row_ptr, col, class_ptr, num_classes, X.err);
+    }
     const int ke = gdi_launch_grid_anneal(P, R, X, spins, nblk, spc, wpc, smem, nullptr, nullptr, st);
     if (ke) return gdi_set_error(GDI_ERR_CUDA, std::string("gdi_anneal_static launch: ") +
                                                    cudaGetErrorString((cudaError_t)ke));

@@ -92,3 +92,47 @@ def test_rejects_bad_model(lib):
         with pytest.raises(P.GdiError) as e:
             _create(g, **kw)
         assert e.value.code == -1
+
+
+def test_rank_space_helper_matches_its_definition(lib):
+    """gdi_rank_space: classes by colour, inside a class by splitmix64 of the vertex id; rank-space
+    CSR with the weight sign in bit 31 (derived here independently of the library)."""
+    import oracle
+    from gdi_synth import splitmix64
+    g = erdos_renyi(400, 0.04, 21, signed=True)
+    rs = P.rank_space(g)
+    color = oracle.greedy_color(g)
+    vert = np.lexsort((splitmix64(np.arange(g.n, dtype=np.uint64)), color))
+    assert np.array_equal(rs.vert_of, vert)
+    counts = np.bincount(color)
+    assert np.array_equal(rs.class_ptr, np.concatenate([[0], np.cumsum(counts[counts > 0])]))
+    assert rs.max_class == counts.max() and rs.max_degree == np.diff(g.row_ptr).max()
+    rank = np.empty(g.n, np.int64)
+    rank[vert] = np.arange(g.n)
+    for r in (0, 17, 399):
+        v = vert[r]
+        nb = g.col[g.row_ptr[v]:g.row_ptr[v + 1]]
+        w = g.w[g.row_ptr[v]:g.row_ptr[v + 1]]
+        exp = rank[nb].astype(np.uint32) | np.where(w < 0, 0x80000000, 0).astype(np.uint32)
+        assert np.array_equal(rs.col[rs.row_ptr[r]:rs.row_ptr[r + 1]], exp)
+    bad = from_edges(3, np.array([0]), np.array([1]))
+    bad.col = bad.col.copy()
+    bad.col[0] = 0
+    with pytest.raises(P.GdiError):
+        P.rank_space(bad)
+
+
+def test_table_helper_matches_the_oracle_table(lib):
+    """gdi_build_table equals the oracle's table (Metropolis rows dE = 1.. while non-zero; paper rows
+    thr(-1, 0, +1))."""
+    import oracle
+    tab, off, temp, mr = P.build_table(P.Schedule(sweeps=40, t0=12.0, t1=0.2))
+    ecap, thr = oracle.table(oracle.METROPOLIS, 12.0, 0.2, 0, 0, 40)
+    for s in range(40):
+        row = thr[s, ecap + 1:]
+        assert np.array_equal(tab[off[s]:off[s + 1]], row[row > 0].astype(np.uint32))
+        assert temp[s] == np.float32(12.0 * (0.2 / 12.0) ** (s / 39))
+    assert mr == max(np.diff(off))
+    tab, off, temp, mr = P.build_table(P.Schedule(sweeps=10, mode=P.GDI_PAPER_PF, pf0=0.2, pf1=0.01))
+    _, thr = oracle.table(oracle.PAPER_PF, 0, 0, 0.2, 0.01, 10)
+    assert mr == 3 and np.array_equal(tab.reshape(10, 3), thr.astype(np.uint32))

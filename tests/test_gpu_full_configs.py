@@ -71,10 +71,9 @@ def _replay_from(g, init, k0, k1, last, kw):
         return pool.map(_replay_job, [(g, init[r], k0, k1, last, r, kw) for r in range(8)])
 
 
-@pytest.mark.skipif(not __import__("os").environ.get("GDI_FULL_REPLAY"),
-                    reason="about 5 minutes of oracle time on 8 cores; set GDI_FULL_REPLAY=1")
 def test_ba1m_all_500_sweeps_every_replica(gdi):
-    """The whole 500-sweep anneal of all 8 replicas replayed by the oracle."""
+    """The whole 500-sweep anneal of all 8 replicas replayed by the oracle (about 5 minutes of
+    oracle time on 8 host cores): every sweep's digest, G and cut, then the repair and every spin."""
     g = barabasi_albert(1_000_000, 5, 4004)
     kw = dict(A=1, B=4, W=256, t0=12.0, t1=0.2, sweeps=500, seed=1)
     ann = gdi.Annealer(g, A=1, B=4, W=256, replicas=8)

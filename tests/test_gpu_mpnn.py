@@ -109,3 +109,37 @@ def test_training_reduces_loss_and_prediction_anneals(setup, gdi):
         assert abs(int(sh[gp[g]:gp[g + 1]].astype(np.int64).sum())) == (gp[g + 1] - gp[g]) % 2
     cut, spins, ms = learn.anneal_batch(gs, sweeps=50, t0=0.5, t1=0.05, seed=5, replicas=1, init=s)
     assert np.all(np.isfinite(cut)) and ms > 0
+
+
+def test_shipped_settings_features_logits_gradients_vs_fp64(gdi):
+    """The settings the warm start ships with: 16 graphs of the recipe (n in [1000, 5000], half
+    Erdos-Renyi, half random geometric; held-out seeds), 256 lazy-walk diffusion steps of the noise
+    channels.  GPU features (FP32 diffusion) against the FP64 oracle; logits from the GPU's own
+    features within 1e-2 of the FP64 forward on the FP64 features; gradients of one batch."""
+    import torch
+    from paper_1908_00210_gb300 import learn
+    gs = learn.make_graphs(16, 900000)
+    ids = np.arange(900000, 900016, dtype=np.uint32)
+    b = learn.GraphBatch.from_graphs(gs, graph_ids=ids)
+    gp, u = batch_union(gs)
+    model = learn.MPNN(seed=21, lam=0.1, feat_seed=0x9E3779B9, steps=256)
+    X = model.features(b)
+    Xr = ref.features(gp, ids, u.row_ptr, u.col, 0x9E3779B9, 256)
+    ferr = np.max(np.abs(X.cpu().numpy() - Xr))
+    assert ferr < 1e-3, ferr
+    z, cache = model.forward(b, X)
+    P = ref.effective_params(model.params.cpu().numpy())
+    zr, cr = ref.forward(P, u.row_ptr, u.col, Xr)
+    zerr = np.max(np.abs(z.cpu().numpy() - zr))
+    assert zerr < 1e-2, zerr
+    rng = np.random.default_rng(3)
+    y = np.empty(gp[-1], dtype=np.int8)
+    for g in range(len(gs)):
+        n = gp[g + 1] - gp[g]
+        y[gp[g]:gp[g + 1]] = rng.permutation(np.where(np.arange(n) < n // 2, 1, -1))
+    loss, _ = model.loss_and_backward(b, torch.from_numpy(y).cuda(), z, cache)
+    Lr, dzr, _ = ref.loss(gp, zr, y, model.lam)
+    gr = ref.flat_grads(ref.backward(P, u.row_ptr, u.col, cr, dzr))
+    assert abs(float(loss.item()) - Lr) < 1e-4 * max(1.0, abs(Lr))
+    g = model.grads.cpu().numpy()
+    assert np.max(np.abs(g - gr)) < 2e-3 * np.max(np.abs(gr))
