@@ -545,7 +545,8 @@ __device__ void estar_ahead(const GridArgs &A, const uint32_t *row, int32_t a0, 
 __device__ void range_thresholds(const GridArgs &A, const GSmem &S, int32_t a0, int32_t a1, int sw,
                                  bool all_reps, int one, int32_t *gam_out, int gis, int grs, uint8_t *s0_out,
                                  int16_t *hbuf, int32_t rlen, float Tsw, bool quad_rows = false,
-                                 const int16_t *es_in = nullptr, int es_s = 0)
+                                 const int16_t *es_in = nullptr, int es_s = 0, int32_t *gc_out = nullptr,
+                                 int32_t gc_val = 0)
 {
     const GdiDevProblem &P = A.P;
     const int64_t base = P.node_off[0];
@@ -556,15 +557,37 @@ __device__ void range_thresholds(const GridArgs &A, const GSmem &S, int32_t a0, 
     if (threadIdx.x == 0) nlong = 0;
     __syncthreads();
     const bool kept = all_reps && A.hf != nullptr;
-    for (int32_t i = threadIdx.x; i < ns; i += GB) {
+    if (kept) {
+        // kept fields: the start signs and field words of up to KU ranks per thread are all in
+        // flight before any is used (one L2 round trip instead of one per rank)
+        constexpr int KU = 2;
+        const ulonglong2 *hf2 = reinterpret_cast<const ulonglong2 *>(A.hf) + base + a0;
+        for (int32_t i0 = threadIdx.x; i0 < ns; i0 += KU * GB) {
+            uint8_t b[KU];
+            ulonglong2 v[KU];
+#pragma unroll
+            for (int u = 0; u < KU; ++u) {
+                const int32_t i = i0 + u * GB;
+                if (i < ns) {
+                    b[u] = __ldcg(packed + base + a0 + i);
+                    v[u] = __ldcg(hf2 + i);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < KU; ++u) {
+                const int32_t i = i0 + u * GB;
+                if (i < ns) {
+                    s0_out[i] = b[u];
+                    const uint2 lo = field_unword(v[u].x), hi = field_unword(v[u].y);
+                    *reinterpret_cast<uint4 *>(hbuf + (size_t)i * 8) = make_uint4(lo.x, lo.y, hi.x, hi.y);
+                }
+            }
+        }
+    }
+    if (gc_out) gc_out[threadIdx.x] = gc_val;       // the caller's thread t < replicas stores word t
+    for (int32_t i = threadIdx.x; i < ns && !kept; i += GB) {
         const int32_t rk = a0 + i;
         s0_out[i] = __ldcg(packed + base + rk);
-        if (kept) {
-            const ulonglong2 v = __ldcg(reinterpret_cast<const ulonglong2 *>(A.hf) + base + rk);
-            const uint2 lo = field_unword(v.x), hi = field_unword(v.y);
-            *reinterpret_cast<uint4 *>(hbuf + (size_t)i * 8) = make_uint4(lo.x, lo.y, hi.x, hi.y);
-            continue;
-        }
         const int64_t e0 = P.row_ptr[base + rk], e1 = P.row_ptr[base + rk + 1];
         if (all_reps && e1 - e0 > LONG_ROW) {
             S.longq[atomicAdd(&nlong, 1)] = i;
@@ -1401,8 +1424,9 @@ __global__ void __launch_bounds__(GB, 1) gdi_grid_sorted_kernel(GridArgs A)
     if (!grid_sync(X)) return;
     __shared__ int npush;
 
-    // my ranks [x0, x1) of class cc
-    auto class_range = [&](int cc, int32_t &x0, int32_t &x1, int &nw) {
+    // my ranks [x0, x1) of class cc (kept in shared memory for the first CB_MAX classes, so that a
+    // class starts without a global round trip for its bounds)
+    auto class_range_g = [&](int cc, int32_t &x0, int32_t &x1, int &nw) {
         const int32_t lo = cls[cc], hi = cls[cc + 1];
         if (A.wbnd) {
             const int32_t *bd = A.wbnd + (size_t)cc * (Pb + 1);
@@ -1411,6 +1435,25 @@ __global__ void __launch_bounds__(GB, 1) gdi_grid_sorted_kernel(GridArgs A)
             nw = bd[p + 1] - bd[p];
         } else {
             class_partition(lo, hi, W, p, Pb, x0, x1, nw);
+        }
+    };
+    constexpr int CB_MAX = 64;
+    __shared__ int32_t cbnd[3 * CB_MAX];
+    for (int cc = threadIdx.x; cc < ncls && cc < CB_MAX; cc += GB) {
+        int32_t x0, x1;
+        int nw;
+        class_range_g(cc, x0, x1, nw);
+        cbnd[3 * cc] = x0;
+        cbnd[3 * cc + 1] = x1;
+        cbnd[3 * cc + 2] = nw;
+    }
+    auto class_range = [&](int cc, int32_t &x0, int32_t &x1, int &nw) {
+        if (cc < CB_MAX) {
+            x0 = cbnd[3 * cc];
+            x1 = cbnd[3 * cc + 1];
+            nw = cbnd[3 * cc + 2];
+        } else {
+            class_range_g(cc, x0, x1, nw);
         }
     };
     uint32_t epoch = 0;
@@ -1429,12 +1472,14 @@ __global__ void __launch_bounds__(GB, 1) gdi_grid_sorted_kernel(GridArgs A)
             int nwin;
             class_range(c, a0, a1, nwin);
             const int32_t ns = a1 - a0;
-            if (threadIdx.x < nrep) Gc[threadIdx.x] = *(volatile int32_t *)&X.Gcls[threadIdx.x];
+            // the class-start G (written by the last block of the previous class) is loaded here
+            // and stored inside the threshold phase, so its round trip overlaps the field loads
+            const int32_t gcl = threadIdx.x < nrep ? *(volatile int32_t *)&X.Gcls[threadIdx.x] : 0;
             // ---- thresholds of my ranks (ends with a block barrier)
             // thresholds of rank a0 + i for replica r at gamc[r * gs + i]
             int32_t *gamc = gam + (a0 & 3);
             range_thresholds(A, S, a0, a1, sw, true, 0, gamc, 1, L.gs, s0, hb, rlen, Tsw, true,
-                             have_es ? esb : nullptr, L.es);
+                             have_es ? esb : nullptr, L.es, threadIdx.x < nrep ? Gc : nullptr, gcl);
             // ---- sorted groups: rel values and stage maps of every (window, replica)
             for (int task = warp; task < nwin * nrep; task += NWARP) {
                 const int kk = task / nrep, r = task % nrep;
@@ -1622,8 +1667,19 @@ __global__ void __launch_bounds__(GB, 1) gdi_grid_sorted_kernel(GridArgs A)
             // neighbours: a warp takes 32 consecutive ranks and walks the concatenated rows of its
             // flipping ones lane by lane (rows longer than LONG_ROW go to a block queue instead)
             uint32_t *pq = reinterpret_cast<uint32_t *>(S.longq);
+            // row bounds of the next chunk are loaded while the current one is pushed
+            int64_t nrow0 = 0, nrow1 = 0;
+            if (A.hf && warp * 32 + lane < ns) {
+                nrow0 = __ldg(P.row_ptr + base + a0 + warp * 32 + lane);
+                nrow1 = __ldg(P.row_ptr + base + a0 + warp * 32 + lane + 1);
+            }
             for (int32_t i0 = warp * 32; i0 < ns; i0 += GB) {
                 const int32_t i = i0 + lane;
+                const int64_t row0 = nrow0, row1 = nrow1;
+                if (A.hf && i + GB < ns) {
+                    nrow0 = __ldg(P.row_ptr + base + a0 + i + GB);
+                    nrow1 = __ldg(P.row_ptr + base + a0 + i + GB + 1);
+                }
                 uint32_t f = 0;
                 if (i < ns) {
                     f = (fm[i >> 2] >> (8 * (i & 3))) & 0xFFu;
@@ -1635,8 +1691,8 @@ __global__ void __launch_bounds__(GB, 1) gdi_grid_sorted_kernel(GridArgs A)
                 int32_t d = 0;
                 unsigned long long d0 = 0, d1 = 0;
                 if (f) {
-                    e0 = P.row_ptr[base + a0 + i];
-                    d = (int32_t)(P.row_ptr[base + a0 + i + 1] - e0);
+                    e0 = row0;
+                    d = (int32_t)(row1 - row0);
                     if (d > LONG_ROW) {
                         pq[atomicAdd(&npush, 1)] = (uint32_t)i | (f << 24);
                         d = 0;
@@ -2003,6 +2059,8 @@ int gdi_grid_plan(const GdiDevProblem &P, int max_row, int sms, size_t smem_limi
                   size_t *smem)
 {
     if (P.num_instances != 1 || P.W < 1) return -1;
+    // the kernels' static shared memory (class bounds, a few words) counts against the same limit
+    smem_limit = smem_limit > 2048 ? smem_limit - 2048 : 0;
     // windows per block under an even split: the largest class decides
     const int wp = (int)((P.max_class + P.W - 1) / P.W);
     const int w = (wp + sms - 1) / sms;
