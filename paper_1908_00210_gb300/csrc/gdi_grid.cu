@@ -1087,7 +1087,7 @@ __host__ __device__ inline int walk_slots(int P) { return nruns(P) + 2 * RUN; }
 struct StageMap {
     unsigned long long mask;            // bit j: the step from lattice point j to j + 1 rises
     int32_t ylo;                        // output index of lattice point 0
-    int32_t pad;
+    int32_t narrow;                     // 1: the window's rel values are exact on the lattice only
 };
 
 struct SortedLayout {
@@ -1211,70 +1211,208 @@ __device__ __forceinline__ void warp_bitonic(uint32_t (&key)[S])
     }
 }
 
+// The same ascending network on 16-bit keys packed two to a register: register t of a lane holds
+// its element t (low half) and element t + S/2 (high half), so a compare-exchange of two registers
+// in the same half does two element pairs at once (__vminu2 / __vmaxu2) and a cross-lane stage
+// moves two keys per shuffle.  Pairs that meet inside one register (the top bit of the in-lane
+// index) are swapped into place with a byte permute.  S >= 2.
+__device__ __forceinline__ uint32_t swap16(uint32_t v) { return __byte_perm(v, 0, 0x1032); }
+
+// compare-exchange of the two halves of v: the minimum to the low half
+__device__ __forceinline__ uint32_t ce_halves(uint32_t v)
+{
+    const uint32_t w = swap16(v);
+    return __byte_perm(__vminu2(v, w), __vmaxu2(v, w), 0x7610);
+}
+
+template <int S>
+__device__ __forceinline__ void warp_bitonic16(uint32_t (&P)[S / 2])
+{
+    constexpr int H = S / 2;
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int size = 2; size <= 32 * S; size <<= 1) {
+        // flip stage: element e meets e ^ (size - 1), the minimum goes to the lower one
+        if (size <= H) {
+#pragma unroll
+            for (int t = 0; t < H; ++t) {
+                if ((t & (size >> 1)) == 0) {
+                    const int q = t ^ (size - 1);
+                    const uint32_t a = P[t], b = P[q];
+                    P[t] = __vminu2(a, b);
+                    P[q] = __vmaxu2(a, b);
+                }
+            }
+        } else if (size == S) {
+            // element t (low half of P[t]) meets S-1-t (high half of P[H-1-t]), and element t + H
+            // (high half of P[t]) meets H-1-t (low half of P[H-1-t])
+#pragma unroll
+            for (int t = 0; t < H; ++t) {
+                const int q = H - 1 - t;
+                if (q == t) {
+                    P[t] = ce_halves(P[t]);
+                } else if (t < q) {
+                    const uint32_t a = P[t], b = swap16(P[q]);
+                    const uint32_t mn = __vminu2(a, b), mx = __vmaxu2(a, b);
+                    P[t] = __byte_perm(mn, mx, 0x7610);
+                    P[q] = __byte_perm(mn, mx, 0x5432);
+                }
+            }
+        } else {
+            const bool lower = ((lane * S) & (size >> 1)) == 0;
+            uint32_t o[H];
+#pragma unroll
+            for (int t = 0; t < H; ++t) o[t] = swap16(__shfl_xor_sync(0xFFFFFFFFu, P[H - 1 - t], size / S - 1));
+#pragma unroll
+            for (int t = 0; t < H; ++t) P[t] = lower ? __vminu2(P[t], o[t]) : __vmaxu2(P[t], o[t]);
+        }
+        // half-cleaners: element e meets e ^ j
+#pragma unroll
+        for (int j = size >> 2; j >= 1; j >>= 1) {
+            if (j >= S) {
+                const bool keep_min = ((lane * S) & j) == 0;
+#pragma unroll
+                for (int t = 0; t < H; ++t) {
+                    const uint32_t o = __shfl_xor_sync(0xFFFFFFFFu, P[t], j / S);
+                    P[t] = keep_min ? __vminu2(P[t], o) : __vmaxu2(P[t], o);
+                }
+            } else if (j == H) {
+#pragma unroll
+                for (int t = 0; t < H; ++t) P[t] = ce_halves(P[t]);
+            } else {
+#pragma unroll
+                for (int t = 0; t < H; ++t) {
+                    if ((t & j) == 0) {
+                        const uint32_t a = P[t], b = P[t + j];
+                        P[t] = __vminu2(a, b);
+                        P[t + j] = __vmaxu2(a, b);
+                    }
+                }
+            }
+        }
+    }
+}
+
 // rel values and the two stage maps of one window (positions [ws, ws + wlen), wlen <= 32 * S) for
 // replica r, by one warp.  out[0] = +1 group, out[1] = -1 group.
+//
+// Narrow keys: when every member has d >= -62 (d = the threshold's distance from c in sort
+// direction), the window sorts 16-bit keys (group, d clamped to [-62, 65] in 7 bits, position).
+// With d >= -62 a window entered at x = G - c in the lattice [-64, 62] keeps x in [-64, 64]
+// through both of its groups (the +1 group cannot take x below -64, the -1 group not above 64), and
+// a member clamped at the top cannot flip at any such x (+1: rel = d + 2k >= 65 > 64; -1:
+// rel = -d - 2k <= -65 < -64) and sorts after every other member of its group either way.  So the
+// stage maps and the replay of a window entered on the lattice are exact; the stored rel values of
+// clamped members are not, so the replay uses a narrow window's rel values only when it is entered
+// on the lattice (StageMap.narrow) and replays it exactly otherwise.
 template <int S>
 __device__ __forceinline__ void window_maps(const int32_t *gam_r, const uint8_t *s0, int16_t *rel_r, int ws,
                                             int wlen, int r, int32_t c, StageMap *out)
 {
     const int lane = threadIdx.x & 31;
-    uint32_t key[S];
+    int32_t dv[S];
+    uint32_t ng = 0;                      // bit s: member s is in the -1 group
     int32_t np = 0;
+    bool wide = false;
 #pragma unroll
     for (int s = 0; s < S; ++s) {
         const int pos = s * 32 + lane;
-        uint32_t k = 0xFFFFFFFFu;
+        dv[s] = 0;
         if (pos < wlen) {
             const int32_t g = gam_r[ws + pos];
             const uint32_t neg = (s0[ws + pos] >> r) & 1u;
             int32_t d = neg ? c - g : g - c;
             d = min(max(d, -KEY_D), KEY_D - 1);
-            k = (neg << 31) | ((uint32_t)(d + KEY_D) << 8) | (uint32_t)pos;
+            dv[s] = d;
+            ng |= neg << s;
             np += neg ? 0 : 1;
+            wide |= d < -62;
         }
-        key[s] = k;
     }
     np = __reduce_add_sync(0xFFFFFFFFu, np);
-    warp_bitonic<S>(key);
-    uint32_t kp0 = 0, kp1 = 0, km0 = 0, km1 = 0;
+    const bool narrow = S >= 2 && !__any_sync(0xFFFFFFFFu, wide);
+    unsigned long long kp = 0, km = 0;
     int32_t cle = 0, cge = 0;
+    // element e of the sorted order: group, d and position -> rel value and lattice bits, without
+    // branches (the lanes of a warp hold members of both groups at every distance)
+    auto take = [&](int e, bool neg, int32_t d, int pos) {
+        const int32_t rel = neg ? -d - 2 * (e - np) : d + 2 * e;
+        rel_r[ws + pos] = (int16_t)min(max(rel, -REL_CAP), REL_CAP);
+        // +1 group: an a_k at or below the lattice start counts into ylo, one in (-64, 62] clears
+        // the step of its lattice interval; -1 group: b_k >= -64 counts, b_k in [-64, 61] clears
+        const bool pos_grp = !neg;
+        cle += (pos_grp && rel <= -NT) ? 1 : 0;
+        const bool p_in = pos_grp && rel > -NT && rel <= NT - 2;
+        kp |= p_in ? 1ull << (((uint32_t)(rel + NT - 1) >> 1) & 63u) : 0ull;
+        const bool m_ge = neg && rel >= -NT;
+        cge += m_ge ? 1 : 0;
+        km |= (m_ge && rel <= NT - 3) ? 1ull << (((uint32_t)(rel + NT) >> 1) & 63u) : 0ull;
+    };
+    if constexpr (S >= 2) {
+        if (narrow) {
+            constexpr int H = S / 2;
+            uint32_t P[H];
 #pragma unroll
-    for (int s = 0; s < S; ++s) {
-        const int e = lane * S + s;
-        if (e < wlen) {
-            const uint32_t k = key[s];
-            const bool neg = (k >> 31) != 0;
-            const int32_t d = (int32_t)((k >> 8) & 0x7FFFFFu) - KEY_D;
-            const int pos = (int)(k & 0xFFu);
-            const int32_t rel = neg ? -d - 2 * (e - np) : d + 2 * e;
-            rel_r[ws + pos] = (int16_t)min(max(rel, -REL_CAP), REL_CAP);
-            if (!neg) {
-                if (rel <= -NT) {
-                    ++cle;
-                } else if (rel <= NT - 2) {
-                    const int b = (rel + NT - 1) >> 1;
-                    if (b < 32) kp0 |= 1u << b; else kp1 |= 1u << (b - 32);
+            for (int t = 0; t < H; ++t) {
+                uint32_t k2[2];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int s = t + h * H;
+                    const int pos = s * 32 + lane;
+                    uint32_t k = 0xFFFFu;
+                    if (pos < wlen) {
+                        const uint32_t neg = (ng >> s) & 1u;
+                        const int32_t dq = min(dv[s], 65) + 62;
+                        k = (neg << 15) | ((uint32_t)dq << 8) | (uint32_t)pos;
+                    }
+                    k2[h] = k;
                 }
-            } else if (rel >= -NT) {
-                ++cge;
-                if (rel <= NT - 3) {
-                    const int b = (rel + NT) >> 1;
-                    if (b < 32) km0 |= 1u << b; else km1 |= 1u << (b - 32);
+                P[t] = k2[0] | (k2[1] << 16);
+            }
+            warp_bitonic16<S>(P);
+#pragma unroll
+            for (int s = 0; s < S; ++s) {
+                const int e = lane * S + s;
+                if (e < wlen) {
+                    const uint32_t k = (s < H ? P[s] : (P[s - H] >> 16)) & 0xFFFFu;
+                    const bool neg = (k >> 15) != 0;
+                    const int32_t d = (int32_t)((k >> 8) & 0x7Fu) - 62;
+                    take(e, neg, d, (int)(k & 0xFFu));
                 }
             }
         }
     }
-    kp0 = __reduce_or_sync(0xFFFFFFFFu, kp0);
-    kp1 = __reduce_or_sync(0xFFFFFFFFu, kp1);
-    km0 = __reduce_or_sync(0xFFFFFFFFu, km0);
-    km1 = __reduce_or_sync(0xFFFFFFFFu, km1);
+    if (!narrow) {
+        uint32_t key[S];
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            const int pos = s * 32 + lane;
+            key[s] = pos < wlen ? (((ng >> s) & 1u) << 31) | ((uint32_t)(dv[s] + KEY_D) << 8) | (uint32_t)pos
+                                : 0xFFFFFFFFu;
+        }
+        warp_bitonic<S>(key);
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            const int e = lane * S + s;
+            if (e < wlen) {
+                const uint32_t k = key[s];
+                take(e, (k >> 31) != 0, (int32_t)((k >> 8) & 0x7FFFFFu) - KEY_D, (int)(k & 0xFFu));
+            }
+        }
+    }
+    const uint32_t kp0 = __reduce_or_sync(0xFFFFFFFFu, (uint32_t)kp);
+    const uint32_t kp1 = __reduce_or_sync(0xFFFFFFFFu, (uint32_t)(kp >> 32));
+    const uint32_t km0 = __reduce_or_sync(0xFFFFFFFFu, (uint32_t)km);
+    const uint32_t km1 = __reduce_or_sync(0xFFFFFFFFu, (uint32_t)(km >> 32));
     cle = __reduce_add_sync(0xFFFFFFFFu, cle);
     cge = __reduce_add_sync(0xFFFFFFFFu, cge);
     if (lane == 0) {
         out[0].mask = ~(((unsigned long long)kp1 << 32) | kp0) & STEP_MASK;
         out[0].ylo = -cle;
+        out[0].narrow = narrow ? 1 : 0;
         out[1].mask = ~(((unsigned long long)km1 << 32) | km0) & STEP_MASK;
         out[1].ylo = cge;
+        out[1].narrow = narrow ? 1 : 0;
     }
 }
 
@@ -1374,6 +1512,64 @@ __device__ __noinline__ int32_t window_replay_exact(const int32_t *gr, const uin
     g = plus_first ? g - 2 * K1 : g + 2 * K1;
     const int32_t K2 = warp_group(gr, 1, 0, s0, r, ws, we, g, !plus_first, bins, fm);
     return plus_first ? g + 2 * K2 : g - 2 * K2;
+}
+
+// Replay of one window (positions [ws, we)) of replica r from x = G - c with its rel values, by one
+// warp: both groups in order, each member deciding by one comparison; the flips go into the
+// replica's flip bitmap fb.  With W a multiple of 32 every window owns whole words; otherwise
+// windows share words and OR their bits in atomically, so windows may be replayed concurrently.
+// Returns x after the window.
+template <int SL>
+__device__ __forceinline__ int32_t replay_window(const int16_t *rr, const uint8_t *s0, int r, int ws, int we,
+                                                 int32_t x, bool plus_first, uint32_t *fb, int W)
+{
+    const int lane = threadIdx.x & 31;
+    // members of the window in registers (slot s = positions ws + 32 s + lane)
+    int32_t rv[SL];
+    uint32_t ng = 0, vd = 0;            // bit s: member is -1 / exists
+#pragma unroll
+    for (int s = 0; s < SL; ++s) {
+        const int i = ws + 32 * s + lane;
+        rv[s] = 0;
+        if (i < we) {
+            rv[s] = rr[i];
+            vd |= 1u << s;
+            ng |= ((uint32_t)(s0[i] >> r) & 1u) << s;
+        }
+    }
+    uint32_t wbits[SL];
+#pragma unroll
+    for (int s = 0; s < SL; ++s) wbits[s] = 0;
+#pragma unroll
+    for (int ph = 0; ph < 2; ++ph) {
+        const bool plus = plus_first == (ph == 0);
+        int32_t cnt = 0;
+#pragma unroll
+        for (int s = 0; s < SL; ++s) {
+            const bool mem = ((vd >> s) & 1u) && (((ng >> s) & 1u) != (plus ? 1u : 0u));
+            const bool f = mem && (plus ? rv[s] <= x : rv[s] >= x);
+            const unsigned bm = __ballot_sync(0xFFFFFFFFu, f);
+            cnt += __popc(bm);
+            wbits[s] |= bm;
+        }
+        x = plus ? x - 2 * cnt : x + 2 * cnt;
+    }
+    // flip words: slot s covers positions [ws + 32 s, ws + 32 s + 32)
+    if ((W & 31) == 0) {
+#pragma unroll
+        for (int s = 0; s < SL; ++s)
+            if (lane == s && ws + 32 * s < we) fb[(ws >> 5) + s] = wbits[s];
+    } else if (lane == 0) {
+        const int sh = ws & 31;
+#pragma unroll
+        for (int s = 0; s < SL; ++s) {
+            if (!wbits[s]) continue;
+            const int q = (ws >> 5) + s;
+            atomicOr(&fb[q], wbits[s] << sh);
+            if (sh) atomicOr(&fb[q + 1], wbits[s] >> (32 - sh));
+        }
+    }
+    return x;
 }
 
 // SL = members per lane of a window sort (1, 2, 4 or 8): one instantiation per window size class
@@ -1588,55 +1784,11 @@ __global__ void __launch_bounds__(GB, 1) gdi_grid_sorted_kernel(GridArgs A)
                     int32_t *bins = hist + (size_t)warp * HA;
                     for (int kk = 0; kk < nwin; ++kk) {
                         const int ws = kk * W, we = min(ws + W, ns);
-                        if (x >= -FAST_X && x <= FAST_X) {
-                            // members of the window in registers (slot s = positions ws + 32 s + lane)
-                            int32_t rv[SL];
-                            uint32_t ng = 0, vd = 0;            // bit s: member is -1 / exists
-#pragma unroll
-                            for (int s = 0; s < SL; ++s) {
-                                const int i = ws + 32 * s + lane;
-                                rv[s] = 0;
-                                if (i < we) {
-                                    rv[s] = rr[i];
-                                    vd |= 1u << s;
-                                    ng |= ((uint32_t)(s0[i] >> r) & 1u) << s;
-                                }
-                            }
-                            uint32_t wbits[SL];
-#pragma unroll
-                            for (int s = 0; s < SL; ++s) wbits[s] = 0;
-#pragma unroll
-                            for (int ph = 0; ph < 2; ++ph) {
-                                const bool plus = plus_first == (ph == 0);
-                                int32_t cnt = 0;
-#pragma unroll
-                                for (int s = 0; s < SL; ++s) {
-                                    const bool mem = ((vd >> s) & 1u) && (((ng >> s) & 1u) != (plus ? 1u : 0u));
-                                    const bool f = mem && (plus ? rv[s] <= x : rv[s] >= x);
-                                    const unsigned bm = __ballot_sync(0xFFFFFFFFu, f);
-                                    cnt += __popc(bm);
-                                    wbits[s] |= bm;
-                                }
-                                x = plus ? x - 2 * cnt : x + 2 * cnt;
-                            }
-                            // flip words: slot s covers positions [ws + 32 s, ws + 32 s + 32)
-                            if ((ws & 31) == 0) {
-#pragma unroll
-                                for (int s = 0; s < SL; ++s)
-                                    if (lane == s && ws + 32 * s < we) fb[(ws >> 5) + s] = wbits[s];
-                            } else if (lane == 0) {
-                                const int sh = ws & 31;
-#pragma unroll
-                                for (int s = 0; s < SL; ++s) {
-                                    if (!wbits[s]) continue;
-                                    const int q = (ws >> 5) + s;
-                                    fb[q] |= wbits[s] << sh;
-                                    fb[q + 1] |= wbits[s] >> (32 - sh);
-                                }
-                            }
-                        } else {
-                            x = window_replay_exact(gr, s0, r, ws, we, c0 + x, plus_first, bins, fm) - c0;
-                        }
+                        // a narrow window's rel values hold on the lattice only (see window_maps)
+                        const bool on = smap[((size_t)kk * 8 + r) * 2].narrow ? (x >= -NT && x <= NT - 2)
+                                                                            : (x >= -FAST_X && x <= FAST_X);
+                        x = on ? replay_window<SL>(rr, s0, r, ws, we, x, plus_first, fb, W)
+                               : window_replay_exact(gr, s0, r, ws, we, c0 + x, plus_first, bins, fm) - c0;
                     }
                     const int32_t gout = c0 + x;
                     if (lane == 0) {
