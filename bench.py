@@ -30,25 +30,52 @@ import numpy as np  # noqa: E402
 # Workloads: seeded synthetic stand-ins for the paper's G-set graphs (generators in gdi_synth)
 WORKLOADS = {
     # Barabasi-Albert n = 10^6, m = 5, unit weights, greedy colouring (6 classes), 8 replicas,
-    # 500 sweeps, window W = 256: the grid-scale path (every SM on one graph)
+    # 500 sweeps, window W = 256: the grid-scale path (every SM on one graph).  Algorithmic bytes
+    # of one spin update in the pull form: 4 d (columns) + 4 (row pointer) + d (neighbour spins)
+    # + 2 (own spin read and write) = 56 B for d = 10.  traffic: dram__bytes_read.sum +
+    # dram__bytes_write.sum of one 500-sweep launch of the sweep kernel (ncu), or None when the
+    # kernel changed after the counters were taken.
     "ba1m_r8": dict(kind="ba", n=1_000_000, m=5, gseed=4004, A=1, B=4, W=256, replicas=8,
                     sweeps=500, t0=12.0, t1=0.2, seed=1,
-                    # traffic: dram__bytes_read.sum + dram__bytes_write.sum of one 500-sweep launch
-                    # of gdi_grid_sorted_kernel<8> (ncu, profiles/gdi_grid_sorted_kernel_ba1m_r8.md)
-                    roofline=dict(bound="hbm", bytes_per_update=56, traffic=50145024 + 2043904)),
-    # 2-D torus 100 x 100, +-1 weights, checkerboard colouring, 64 replicas, 5000 sweeps
+                    roofline=dict(bound="hbm", bytes_per_update=56, traffic=None)),
+    # 2-D torus 100 x 100, +-1 weights, checkerboard colouring, 64 replicas, 5000 sweeps: the
+    # CTA-resident path.  26 B per update: 4 x 4 B columns + 4 B row pointer + 4 x 1 B spins + 2 B.
     "torus100_r64": dict(kind="torus", L=100, gseed=2002, A=1, B=4, W=1024, replicas=64,
                          sweeps=5000, t0=12.0, t1=0.2, seed=1,
-                         roofline=dict(bound="alu", ops_per_update=100)),
-    # Erdos-Renyi n = 800, p = 0.06, unit weights, greedy colouring, 1000 sweeps, 1 replica
+                         roofline=dict(bound="hbm", bytes_per_update=26, traffic=None)),
+    # Erdos-Renyi n = 800, p = 0.06, unit weights, greedy colouring, 1000 sweeps, 1 replica: one
+    # block holds the whole instance; latency-bound.  Bytes per update 4 d + 4 + d + 2 at d = 48.7.
     "er800": dict(kind="er", n=800, p=0.06, gseed=1001, A=1, B=4, W=64, replicas=1, sweeps=1000,
-                  t0=12.0, t1=0.2, seed=1, roofline=dict(bound="alu", ops_per_update=300)),
+                  t0=12.0, t1=0.2, seed=1, roofline=dict(bound="hbm", bytes_per_update=249.5, traffic=None)),
+    # 4,096 Erdos-Renyi instances, n ~ U[800, 3000], mean degree ~ U[3, 48], unit or +-1 weights,
+    # one replica each, 2000 sweeps, one persistent launch (CTA-resident, autotuned).  Bytes per
+    # update at the batch's mean degree d = 25.5: 4 d + 4 + d + 2 = 134 B.
+    "batched4096": dict(kind="batch", count=4096, gseed=3000, n_lo=800, n_hi=3000, A=1, B=4, W=256,
+                        replicas=1, sweeps=2000, t0=12.0, t1=0.2, seed=11,
+                        roofline=dict(bound="hbm", bytes_per_update=134, traffic=None)),
 }
 DEFAULT_WORKLOAD = "ba1m_r8"
 
 
+def _er_chunk(args):
+    from gdi_synth import er_batch
+    count, seed0, n_lo, n_hi = args
+    return er_batch(count, seed0, n_lo=n_lo, n_hi=n_hi)
+
+
 def make_graph(wl):
-    from gdi_synth import barabasi_albert, erdos_renyi, torus2d
+    """The workload's graph; for a batch, the disjoint union (with .inst_ptr and .parts)."""
+    from gdi_synth import barabasi_albert, batch_union, erdos_renyi, torus2d
+    if wl["kind"] == "batch":
+        import multiprocessing as mp
+        jobs = [(min(256, wl["count"] - i), wl["gseed"] + i, wl["n_lo"], wl["n_hi"])
+                for i in range(0, wl["count"], 256)]
+        with mp.get_context("spawn").Pool(min(16, len(jobs))) as pool:
+            parts = [g for part in pool.map(_er_chunk, jobs) for g in part]
+        inst_ptr, u = batch_union(parts)
+        u.inst_ptr = inst_ptr
+        u.parts = parts
+        return u
     if wl["kind"] == "ba":
         return barabasi_albert(wl["n"], wl["m"], wl["gseed"])
     if wl["kind"] == "torus":
@@ -122,36 +149,50 @@ class ClockSampler:
 # ---------------------------------------------------------------------------------------------
 def oracle_throughput(g, wl, seconds: float = 12.0, processes: int | None = None):
     """The oracle as it stands, timed on the host cores on a bounded sample of the workload: each
-    worker process anneals 4 replicas of the graph for as many sweeps of the same schedule as fit
-    the time budget (decided from a one-sweep probe).  Returns (updates/s, cores, sample text)."""
+    worker process anneals up to 4 replicas of the graph (for a batch: 4 of its instances, a
+    different set per process) for as many sweeps of the same schedule as fit the time budget
+    (decided from a one-sweep probe).  Returns (updates/s, cores, sample text)."""
     import multiprocessing as mp
     import oracle
     oracle.build()
     cores = processes or os.cpu_count() or 1
     R = min(4, wl["replicas"])
+    parts = getattr(g, "parts", None)
+    sets = [_inst_set(parts, k) for k in range(cores)] if parts else [None] * cores
     t = time.perf_counter()
-    oracle.anneal(g, A=wl["A"], B=wl["B"], W=wl["W"], t0=wl["t0"], t1=wl["t1"], sweeps=wl["sweeps"],
-                  seed=wl["seed"], replicas=R, color=g.color, last_sweep=1, trace=False, repair=False)
+    _oracle_worker((g if parts is None else sets[0], wl, R, 1, 0))
     per_sweep = max(time.perf_counter() - t, 1e-4)
     sweeps = int(max(1, min(wl["sweeps"], seconds / per_sweep)))
     ctx = mp.get_context("spawn")
-    args = [(g, wl, R, sweeps, k) for k in range(cores)]
+    args = [(g if parts is None else sets[k], wl, R, sweeps, k) for k in range(cores)]
     t0 = time.perf_counter()
     with ctx.Pool(cores) as pool:
         pool.map(_oracle_worker, args)
     dt = time.perf_counter() - t0
-    updates = cores * R * sweeps * g.n
-    sample = (f"{cores} processes x {R} replicas x first {sweeps} of {wl['sweeps']} sweeps "
-              f"x {g.n} spins = {updates:.3e} updates in {dt:.1f} s")
+    if parts is None:
+        updates = cores * R * sweeps * g.n
+        sample = (f"{cores} processes x {R} replicas x first {sweeps} of {wl['sweeps']} sweeps "
+                  f"x {g.n} spins = {updates:.3e} updates in {dt:.1f} s")
+    else:
+        spins = sum(sum(x.n for x in st) for st in sets)
+        updates = R * sweeps * spins
+        sample = (f"{cores} processes x 4 instances of the batch x {R} replica x first {sweeps} of "
+                  f"{wl['sweeps']} sweeps ({spins} spins) = {updates:.3e} updates in {dt:.1f} s")
     return updates / dt, cores, sample
+
+
+def _inst_set(parts, k):
+    """Instances 4k .. 4k + 3 of a batch (mod its size): the oracle sample of worker k."""
+    return [parts[(4 * k + j) % len(parts)] for j in range(4)]
 
 
 def _oracle_worker(a):
     g, wl, R, sweeps, k = a
     import oracle
-    oracle.anneal(g, A=wl["A"], B=wl["B"], W=wl["W"], t0=wl["t0"], t1=wl["t1"], sweeps=wl["sweeps"],
-                  seed=wl["seed"] + 1000 * k, replicas=R, color=g.color, last_sweep=sweeps,
-                  trace=False, repair=False)
+    for x in (g if isinstance(g, list) else [g]):
+        oracle.anneal(x, A=wl["A"], B=wl["B"], W=wl["W"], t0=wl["t0"], t1=wl["t1"], sweeps=wl["sweeps"],
+                      seed=wl["seed"] + 1000 * k, replicas=R, color=x.color, last_sweep=sweeps,
+                      trace=False, repair=False)
     return 0
 
 
@@ -206,7 +247,10 @@ def run_reference(args, wl, rank, world):
     updates_per_step = wl["replicas"] * wl["sweeps"] * g.n
     line = {"impl": "reference", "metric": "spin-updates/s", "value": value, "unit": "spin-updates/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * updates_per_step / value, "higher_is_better": True,
+            "ms_per_step": 1e3 * updates_per_step / value,
+            "ms_per_step_note": "extrapolated: the oracle anneals a bounded sample of the step's sweeps and "
+                                "replicas; the whole step at the measured rate",
+            "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
             "config": config_of(args.workload, wl, g),
             "cpu_baseline": {"value": value, "unit": "spin-updates/s", "cores": cores,
@@ -217,11 +261,14 @@ def run_reference(args, wl, rank, world):
 
 
 def config_of(name, wl, g):
-    return {"workload": name, "n": g.n, "nnz": g.nnz, "replicas": wl["replicas"],
-            "sweeps": wl["sweeps"], "A": wl["A"], "B": wl["B"], "W": wl["W"],
-            "schedule": f"metropolis T {wl['t0']}->{wl['t1']} (3.0->0.05 in units of B)",
-            "l2": "L2 flushed (256 MiB write) before every timed step",
-            "parallelism": "replicas"}
+    c = {"workload": name, "n": g.n, "nnz": g.nnz, "replicas": wl["replicas"],
+         "sweeps": wl["sweeps"], "A": wl["A"], "B": wl["B"], "W": wl["W"],
+         "schedule": f"metropolis T {wl['t0']}->{wl['t1']} (3.0->0.05 in units of B)",
+         "l2": "L2 flushed (256 MiB write) before every timed step",
+         "parallelism": "replicas" if wl["kind"] != "batch" else "instances"}
+    if wl["kind"] == "batch":
+        c["instances"] = wl["count"]
+    return c
 
 
 def run_ours(args, wl, rank, world, local):
@@ -235,8 +282,10 @@ def run_ours(args, wl, rank, world, local):
     seed = wl["seed"] + 7919 * rank
     sch = P.Schedule(sweeps=wl["sweeps"], t0=wl["t0"], t1=wl["t1"])
     t_create = time.perf_counter()
-    ann = P.Annealer(g, A=wl["A"], B=wl["B"], W=wl["W"], replicas=wl["replicas"])
+    ann = P.Annealer(g, A=wl["A"], B=wl["B"], W=wl["W"], replicas=wl["replicas"],
+                     inst_ptr=getattr(g, "inst_ptr", None))
     create_s = time.perf_counter() - t_create
+    tuned = ann.autotune(sch, probe_sweeps=20) if wl["kind"] == "batch" else None
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")
     updates = wl["replicas"] * wl["sweeps"] * g.n
 
@@ -316,7 +365,9 @@ def run_ours(args, wl, rank, world, local):
         achieved = rf["bytes_per_update"] * rate / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": rf.get("traffic"),
-                "bytes_per_update": rf["bytes_per_update"], "kernel_ms_per_launch": kernel_ms,
+                "algorithmic_bytes_per_update": rf["bytes_per_update"], "kernel_ms_per_launch": kernel_ms,
+                "achieved_note": "algorithmic bytes (pull-form gather of every update) / sweep-kernel time; "
+                                 "the graph stays L2-resident, so DRAM traffic is far below these bytes",
                 "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
     else:
         sm_max = float(pk.get("sm_max_mhz", 2070.0))
@@ -346,6 +397,7 @@ def run_ours(args, wl, rank, world, local):
         "clocks": clk, "gpu_launches": launches,
         "wall_s_timed_region": wall,
         "launch": launch,
+        "autotune": tuned,
         "create_s": create_s,
         "result": {"final_cut_median": float(np.median(res["final_cut"])),
                    "final_G_max_abs": int(np.abs(res["final_G"]).max()),

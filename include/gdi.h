@@ -67,6 +67,11 @@ extern "C" {
 #define GDI_FLAG_RACY      8  /* Algorithm 3 as printed: inside a colour class every spin decides on
                                  the G it reads at that moment and adds its change with an atomic;
                                  not deterministic, W ignored; grid-scale path (one instance) only */
+#define GDI_FLAG_STANDARD 16  /* Algorithm 2, the paper's "standard" annealer (Section 5.2): every
+                                 spin forms the balance term of Eq. 5 by reading all n spins (the
+                                 complete graph) instead of the decoupled G, and the spins of a
+                                 window decide on the state at the window start (W = 1: one spin at
+                                 a time).  Deterministic; CTA-resident path only */
 
 typedef struct gdi_ctx gdi_ctx;  /* opaque; owned by the library */
 

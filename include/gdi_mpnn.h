@@ -16,8 +16,8 @@
  *
  * Network: H_l = ReLU(H_{l-1} Ws_l + (A_mean H_{l-1}) Wn_l + b_l), l = 1..3, hidden 64,
  * A_mean = D^-1 A; logits z = H_3 wo + bo.  Input features: 16 channels (8 channels of Philox +-1
- * noise diffused by lazy normalised-walk steps, centred and scaled per graph; log(1 + deg);
- * deg / mean degree; 6 zeros).
+ * noise diffused by lazy normalised-walk steps, centred and scaled per graph and optionally
+ * sign-aligned to the first channel; log(1 + deg); deg / mean degree; 6 zeros).
  */
 #ifndef GDI_MPNN_H
 #define GDI_MPNN_H
@@ -33,12 +33,17 @@ extern "C" {
 #define GDI_MPNN_HIDDEN 64
 #define GDI_MPNN_FEATURES 16
 
+/* feature flags */
+#define GDI_MPNN_ALIGN    1   /* noise channel c >= 1 times the sign of its inner product with channel 0 */
+#define GDI_MPNN_NO_NOISE 2   /* the 8 noise channels are 0 (ablation: degree features only)            */
+
 /* Input features X [N x 16].  Vertex i of graph g draws channel c from Philox counter
- * (i - graph_ptr[g], c, graph_id[g], 0x4D504E4E) under key (seed low, seed high), word 0, bit 31.
- * scratch: float [2 * N * 8]. */
+ * (i - graph_ptr[g], c, graph_id[g], 0x4D504E4E) under key (seed low, seed high), word 0, bit 31;
+ * the 8 noise channels are diffused by `steps` lazy walk steps, centred and scaled per graph, and
+ * (GDI_MPNN_ALIGN) sign-aligned to channel 0 per graph.  scratch: float [2 * N * 8]. */
 int gdi_mpnn_features(int64_t N, int32_t G, const int64_t *graph_ptr, const uint32_t *graph_id,
                       const int64_t *row_ptr, const int32_t *col, uint64_t seed, int32_t steps,
-                      float *X, float *scratch, void *stream);
+                      int32_t flags, float *X, float *scratch, void *stream);
 
 /* Y [N x d] (d <= 64) from X [N x d]: mode 0 = A_mean X, mode 1 = A_mean^T X (transpose, used by
  * the backward pass), mode 2 = one lazy normalised-walk step 0.5 X + 0.5 D^-1/2 A D^-1/2 X.

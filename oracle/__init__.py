@@ -61,6 +61,7 @@ class _Params(C.Structure):
         ("last_sweep", C.c_int32),
         ("check_invariants", C.c_int32),
         ("first_replica", C.c_int32),
+        ("stale", C.c_int32),
     ]
 
 
@@ -187,9 +188,11 @@ def anneal(g, *, A: int = 1, B: int = 1, W: int = 0, mode: int = METROPOLIS, t0:
            t1: float = 0.05, pf0: float = 0.2, pf1: float = 0.01, sweeps: int = 100,
            seed: int = 1, instance: int = 0, replicas: int = 1, color=None, init=None,
            first_sweep: int = 0, last_sweep: int = 0, trace: bool = True,
-           check_invariants: bool = False, repair: bool = True, first_replica: int = 0) -> AnnealResult:
+           check_invariants: bool = False, repair: bool = True, first_replica: int = 0,
+           stale: bool = False) -> AnnealResult:
     """Run the oracle annealer on one instance: replicas first_replica .. first_replica + replicas - 1
-    (output row k is replica first_replica + k)."""
+    (output row k is replica first_replica + k).  stale: every spin of a window decides on the G of
+    the window start (the reference of the racy variant) instead of the running G."""
     n = g.n
     rp = np.ascontiguousarray(g.row_ptr, dtype=np.int64)
     cc = np.ascontiguousarray(g.col, dtype=np.int32)
@@ -207,7 +210,7 @@ def anneal(g, *, A: int = 1, B: int = 1, W: int = 0, mode: int = METROPOLIS, t0:
     ctr = np.zeros((replicas, sweeps), dtype=np.int64) if trace else None
     P = _Params(n, _p(rp), _p(cc), _p(ww), _p(colr), A, B, W, mode, t0, t1, pf0, pf1, sweeps,
                 seed & 0xFFFFFFFFFFFFFFFF, instance, replicas, first_sweep, last_sweep,
-                1 if check_invariants else 0, first_replica)
+                1 if check_invariants else 0, first_replica, 1 if stale else 0)
     O = _Out(_p(spins), 1 if init is not None else 0, _p(raw_G), _p(final_G), _p(raw_cut),
              _p(final_cut), _p(dig), _p(gtr), _p(ctr), 0, 0, 1 if repair else 0, 0)
     rc = lib().oracle_anneal(C.byref(P), C.byref(O))

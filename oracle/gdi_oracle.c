@@ -44,6 +44,9 @@
  *       pair (+1,-1) or (-1,+1); an odd last rank starts at -1.
  *   R5  After the last sweep an exact-balance repair flips the k = (|G| - (n mod 2))/2 majority
  *       spins with the smallest (s_i h_i, rank) keys.
+ *   Stale option (the racy variant's reference): every spin of a window decides on the G of the
+ *       window start, as parallel threads that all read G before any flip of the window lands
+ *       (Section 5.3's outdated G); the flips still update G exactly afterwards.
  *
  * Everything is integer except the threshold table, which is built in double precision with
  * exp() and pow() from libm.
@@ -288,6 +291,9 @@ typedef struct {
     int32_t last_sweep;        /* exclusive end; <= 0 means sweeps */
     int32_t check_invariants;  /* recompute G and cut after every window */
     int32_t first_replica;     /* replica index of output row 0 (Philox counter word 3, digest) */
+    int32_t stale;             /* 1: every spin of a window decides on the G of the window start
+                                  (the stale G of Algorithm 3's parallel threads, Section 5.3)
+                                  instead of the running G of R2 */
 } oracle_params;
 
 typedef struct {
@@ -498,7 +504,22 @@ int oracle_anneal(const oracle_params *p, oracle_out *o)
                     /* the two groups of the window, in the canonical order of R2; membership is
                      * the sign at window start, so a spin is decided at most once per sweep */
                     for (int32_t r = wlo; r < whi; ++r) s0[r] = s[r];
-                    for (int ph = 0; ph < 2; ++ph) {
+                    if (p->stale) {
+                        /* stale reading: all spins of the window see the G of the window start,
+                         * as threads that read G before any of the window's atomics land */
+                        const int64_t Gv = G;
+                        for (int32_t r = wlo; r < whi; ++r) {
+                            const int64_t dE = (int64_t)p->B * s0[r] * hbuf[r]
+                                             + 4 * (int64_t)p->A * (1 - (int64_t)s0[r] * Gv);
+                            const int64_t kc = (dE < -ecap ? -ecap : (dE > ecap ? ecap : dE)) + ecap;
+                            if ((uint64_t)ubuf[r] < row[kc]) {
+                                cut += (int64_t)s[r] * hbuf[r];
+                                G -= 2 * (int64_t)s[r];
+                                s[r] = (int8_t)-s[r];
+                            }
+                        }
+                    }
+                    for (int ph = 0; ph < 2 && !p->stale; ++ph) {
                         const int plus_group = ((sw & 1) == 0) ? (ph == 0) : (ph == 1);
                         int32_t m = 0;
                         for (int32_t r = wlo; r < whi; ++r) {

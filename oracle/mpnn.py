@@ -4,7 +4,8 @@ Plain numpy, float64, written from the definitions (no blocking, no fusion), and
 with the CUDA kernels.  The network's weights are taken as BF16 (round-to-nearest-even of the
 float32 master values), exactly as the GPU path uses them; everything else is float64.
 
-    features  X = [diffused Philox +-1 noise (8 channels, centred, unit RMS per graph),
+    features  X = [diffused Philox +-1 noise (8 channels, centred, unit RMS per graph, optionally
+                   sign-aligned to channel 0 per graph),
                    log(1 + deg), deg / mean deg, 0 x 6]
     layer l   H_l = ReLU(H_{l-1} Ws_l + (D^-1 A H_{l-1}) Wn_l + b_l),  l = 1, 2, 3
     logits    z = H_3 wo + bo
@@ -106,7 +107,12 @@ def lazy_walk(row_ptr, col, X, S=None):
 
 
 # ------------------------------------------------------------------ features ------------------
-def features(graph_ptr, graph_id, row_ptr, col, seed, steps):
+ALIGN, NO_NOISE = 1, 2
+
+
+def features(graph_ptr, graph_id, row_ptr, col, seed, steps, flags=0):
+    """Input features; flags & ALIGN: noise channel c >= 1 times the sign of its inner product with
+    channel 0 inside each graph (sign 0 -> +1); flags & NO_NOISE: noise channels 0."""
     N = len(row_ptr) - 1
     R = np.zeros((N, NRAND))
     key = [seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF]
@@ -129,7 +135,12 @@ def features(graph_ptr, graph_id, row_ptr, col, seed, steps):
         s = slice(graph_ptr[g], graph_ptr[g + 1])
         r = R[s] - R[s].mean(axis=0)
         rms = np.sqrt((r ** 2).mean(axis=0)) + 1e-12
-        X[s, :NRAND] = r / rms
+        sign = np.ones(NRAND)
+        if flags & ALIGN:
+            sign[1:] = np.where(r[:, 1:].T @ r[:, 0] < 0, -1.0, 1.0)
+        if flags & NO_NOISE:
+            sign[:] = 0.0
+        X[s, :NRAND] = sign * (r / rms)
         X[s, NRAND] = np.log1p(deg[s])
         md = deg[s].mean()
         X[s, NRAND + 1] = deg[s] / md if md > 0 else 0.0

@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(_PKG, "libgdi.so")
 
 GDI_MEM_HOST, GDI_MEM_DEVICE = 0, 1
 GDI_METROPOLIS, GDI_PAPER_PF = 0, 1
-GDI_FLAG_TRACE, GDI_FLAG_NO_REPAIR, GDI_FLAG_CONTINUE, GDI_FLAG_RACY = 1, 2, 4, 8
+GDI_FLAG_TRACE, GDI_FLAG_NO_REPAIR, GDI_FLAG_CONTINUE, GDI_FLAG_RACY, GDI_FLAG_STANDARD = 1, 2, 4, 8, 16
 
 ERRORS = {
     -1: "GDI_ERR_INVALID_ARG", -2: "GDI_ERR_NOT_SYMMETRIC", -3: "GDI_ERR_SELF_LOOP",

@@ -705,7 +705,8 @@ int gdi_anneal(gdi_ctx *c, const gdi_schedule *S, const gdi_run *run)
     R.key0 = key0;
     R.key1 = key1;
     R.flags = (trace ? GDI_DEV_TRACE : 0) | ((run->flags & GDI_FLAG_NO_REPAIR) ? GDI_DEV_NO_REPAIR : 0) |
-              ((run->flags & GDI_FLAG_RACY) ? GDI_DEV_RACY : 0);
+              ((run->flags & GDI_FLAG_RACY) ? GDI_DEV_RACY : 0) |
+              ((run->flags & GDI_FLAG_STANDARD) ? GDI_DEV_STANDARD : 0);
     R.raw_G = c->raw_G.p;
     R.final_G = c->final_G.p;
     R.raw_cut = c->raw_cut.p;
@@ -724,7 +725,10 @@ int gdi_anneal(gdi_ctx *c, const gdi_schedule *S, const gdi_run *run)
     cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
     bool grid = false;
+    if ((run->flags & GDI_FLAG_STANDARD) && ((run->flags & GDI_FLAG_RACY) || c->path == GDI_PATH_GRID))
+        return fail(GDI_ERR_INVALID_ARG, "GDI_FLAG_STANDARD runs on the CTA-resident path only");
     if (c->path == GDI_PATH_GRID || (run->flags & GDI_FLAG_RACY)) grid = true;
+    else if (run->flags & GDI_FLAG_STANDARD) grid = false;
     else if (c->path == GDI_PATH_AUTO && c->Q == 1 && c->W >= 1 && c->max_degree <= 32767) {
         // one instance: the cheaper path by a cost model fitted on GB300 (BA and ER graphs of mean
         // degree 10, 10^3 to 6.4*10^4 vertices, 1 to 608 replicas).  A CTA-resident sweep costs

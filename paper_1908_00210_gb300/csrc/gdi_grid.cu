@@ -1125,11 +1125,9 @@ __host__ __device__ inline SortedLayout sorted_layout(int spc, int wpc, int max_
 }
 
 // chain buffers carved from the scratch table area: exact outgoing G [P][8] (epoch << 32 | G),
-// two unused flag areas [P] and [NR], block tables [P][8][64], run tables [NR][8][64]
+// block tables [P][8][64], run tables [NR][8][64]
 __host__ __device__ inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
-__host__ __device__ inline size_t chain_off_flag(int P) { return align256((size_t)P * 8 * sizeof(uint64_t)); }
-__host__ __device__ inline size_t chain_off_rflag(int P) { return chain_off_flag(P) + align256((size_t)P * sizeof(uint32_t)); }
-__host__ __device__ inline size_t chain_off_tab(int P) { return chain_off_rflag(P) + align256((size_t)nruns(P) * sizeof(uint32_t)); }
+__host__ __device__ inline size_t chain_off_tab(int P) { return align256((size_t)P * 8 * sizeof(uint64_t)); }
 __host__ __device__ inline size_t chain_off_rtab(int P) { return chain_off_tab(P) + (size_t)P * 8 * NT; }
 __host__ __device__ inline size_t chain_bytes(int P) { return chain_off_rtab(P) + (size_t)nruns(P) * 8 * NT; }
 

@@ -110,6 +110,7 @@ int gdi_launch_gather_spins(const GdiDevProblem &P, const int8_t *spins_rank, in
 #define GDI_DEV_TRACE 1
 #define GDI_DEV_NO_REPAIR 2
 #define GDI_DEV_RACY 4
+#define GDI_DEV_STANDARD 8
 
 // device error codes written to GdiDevRun::err
 #define GDI_DEVERR_RANGE 1

@@ -160,6 +160,39 @@ __device__ void select_and_flip(const Smem &S, int32_t wlo, int32_t Wn, int grp,
     if (threadIdx.x == 0) *S.G = Gc - 2 * grp * K;
 }
 
+// Algorithm 2 (the paper's standard annealer, GDI_FLAG_STANDARD): every spin of the window forms
+// the balance term from the complete graph of Eq. 5, i.e. sums all n spins itself (an O(n) read per
+// spin, which is what the decoupled G of Algorithm 3 removes), on the state at the window start,
+// and flips iff its draw accepts dE = B s h + 4A (1 - s G) -- the same test as "G >= gamma" with
+// the threshold gamma of step 1.  All decisions are taken before any spin of the window changes.
+template <int BS>
+__device__ void standard_window(const Smem &S, int32_t wlo, int32_t Wn, int32_t n)
+{
+    __syncthreads();
+    int32_t dG = 0;
+    // the spin vector is read in 4-byte words from its first 4-byte boundary on (the shared
+    // layout aligns it to 8 bytes only); the bytes before and after are read one by one
+    const int32_t head = (int32_t)((4 - (reinterpret_cast<uintptr_t>(S.sig) & 3)) & 3) < n
+                             ? (int32_t)((4 - (reinterpret_cast<uintptr_t>(S.sig) & 3)) & 3) : n;
+    const int32_t nwords = (n - head) >> 2;
+    const int32_t *sw = reinterpret_cast<const int32_t *>(S.sig + head);
+    for (int32_t p = threadIdx.x; p < Wn; p += BS) {
+        int32_t G = 0;                              // sum of all spins, read by this spin
+        for (int32_t j = 0; j < head; ++j) G += S.sig[j];
+        for (int32_t k = 0; k < nwords; ++k) G += __dp4a(sw[k], 0x01010101, 0);
+        for (int32_t j = head + 4 * nwords; j < n; ++j) G += S.sig[j];
+        const int sg = S.s0[p];
+        const bool flip = sg > 0 ? G >= S.gam[p] : G <= S.gam[p];
+        S.flag[wlo + p] = flip ? 1 : 0;
+        dG += flip ? -2 * sg : 0;
+    }
+    dG = block_sum<BS, int32_t>(dG, S.red32);
+    for (int32_t p = threadIdx.x; p < Wn; p += BS)
+        if (S.flag[wlo + p]) S.sig[wlo + p] = (int8_t)(-S.s0[p]);
+    __syncthreads();
+    if (threadIdx.x == 0) *S.G += dG;
+}
+
 // cut of the item: (1/2) sum_i sum_j w_ij [s_i != s_j]
 template <int BS>
 __device__ int64_t item_cut(const GdiDevProblem &P, int64_t base, int32_t n, const Smem &S)
@@ -313,6 +346,10 @@ __global__ void __launch_bounds__(BS) gdi_cta_anneal_kernel(GdiDevProblem P, Gdi
                             S.gam[r - wlo] = gamma_of(sg, h, es, P.A, P.B);
                             S.s0[r - wlo] = (int8_t)sg;
                         }
+                    }
+                    if (R.flags & GDI_DEV_STANDARD) {
+                        standard_window<BS>(S, wlo, Wn, n);
+                        continue;
                     }
                     // step 2/3: the two groups in the canonical order (+1 first on even sweeps)
                     const int first = (sw & 1) ? -1 : 1;

@@ -4,8 +4,9 @@
 //
 // Layer l: H_l = ReLU(H_{l-1} Ws_l + (A_mean H_{l-1}) Wn_l + b_l), A_mean = D^-1 A (mean over
 // neighbours).  Output z = H_3 wo + bo.  Weights are BF16 (round-to-nearest-even copies of FP32
-// master weights); activations, accumulations and gradients are FP32.  The matrices are tiny
-// (<= 64 x 64), so the dense layers run on CUDA cores with the weights in shared memory; the
+// master weights); activations, accumulations and gradients are FP32.  The dense layers of the
+// network (din = 16 and 64), forward and backward, run on the tensor cores (mma.sync m16n8k16,
+// BF16 operands, FP32 accumulation) with the FP32 activations split into two BF16 parts; the
 // neighbour aggregations are CSR gathers with one warp per vertex and lanes over channels.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -21,6 +22,8 @@ namespace {
 constexpr int HID = GDI_MPNN_HIDDEN;   // 64
 constexpr int FIN = GDI_MPNN_FEATURES; // 16
 constexpr int NRAND = 8;               // random positional channels
+
+inline bool aligned(const void *p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) & (a - 1)) == 0; }
 
 __device__ __forceinline__ float bf16_to_f(uint16_t b)
 {
@@ -134,6 +137,155 @@ __global__ void dense_bwd_kernel(int64_t N, int din, const uint16_t *Ws, const u
         }
         if (lane < din) { dXs[i * din + lane] = s0; T[i * din + lane] = t0; }
         if (lane + 32 < din) { dXs[i * din + lane + 32] = s1; T[i * din + lane + 32] = t1; }
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Tensor-core dense layers (din = 16 or 64): mma.sync m16n8k16 with BF16 operands and FP32
+// accumulation, one warp per tile of 16 vertices.  The weights are BF16 already; an FP32
+// activation x is split into two BF16 parts hi = bf16(x), lo = bf16(x - hi), and hi W + lo W is
+// accumulated in FP32: each product of BF16 values is exact in FP32, so the only rounding beyond
+// the FP32 sums is the part of x below lo (about 2^-17 of |x|).
+// Fragment layout of m16n8k16 (PTX ISA): g = lane / 4, q = lane % 4; A (16 x 16, row major) regs
+// a0..a3 = rows g, g + 8, g, g + 8 at columns 2q, 2q + 1 (a0, a1) and 2q + 8, 2q + 9 (a2, a3);
+// B (16 x 8, column major) regs b0, b1 = rows 2q, 2q + 1 and 2q + 8, 2q + 9 of column g;
+// C/D (16 x 8) c0, c1 = row g, columns 2q, 2q + 1; c2, c3 = row g + 8, same columns.  The lower
+// 16 bits of a register hold the element with the smaller index.
+__device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1)
+{
+    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, "
+                 "{%8, %9}, {%0, %1, %2, %3};\n"
+                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// two FP32 values (element k, k + 1) -> packed BF16 high parts and packed BF16 residuals
+__device__ __forceinline__ void split_bf16x2(float x0, float x1, uint32_t &hi, uint32_t &lo)
+{
+    const __nv_bfloat16 h0 = __float2bfloat16_rn(x0), h1 = __float2bfloat16_rn(x1);
+    const __nv_bfloat16 l0 = __float2bfloat16_rn(x0 - __bfloat162float(h0));
+    const __nv_bfloat16 l1 = __float2bfloat16_rn(x1 - __bfloat162float(h1));
+    hi = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+    lo = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+}
+
+// H = ReLU([X | AGG] [Ws; Wn] + b): K = 2 DIN, 64 outputs = 8 column tiles.
+template <int DIN>
+__global__ void __launch_bounds__(256) dense_fwd_mma_kernel(int64_t N, const float *X, const float *AGG,
+                                                            const uint16_t *Ws, const uint16_t *Wn,
+                                                            const float *b, float *H)
+{
+    constexpr int K = 2 * DIN, KP = K / 2 + 4;           // pairs per output column (+4: banks)
+    __shared__ uint32_t wt[HID * KP];                     // [n][k pair]: (k, k+1) of output n
+    for (int t = threadIdx.x; t < HID * (K / 2); t += blockDim.x) {
+        const int n = t / (K / 2), kp = t % (K / 2), k = 2 * kp;
+        const uint16_t w0 = k < DIN ? Ws[k * HID + n] : Wn[(k - DIN) * HID + n];
+        const uint16_t w1 = k + 1 < DIN ? Ws[(k + 1) * HID + n] : Wn[(k + 1 - DIN) * HID + n];
+        wt[n * KP + kp] = (uint32_t)w0 | ((uint32_t)w1 << 16);
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
+    const int64_t wglob = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    float bias[8][2];
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) { bias[nt][0] = b[nt * 8 + 2 * q]; bias[nt][1] = b[nt * 8 + 2 * q + 1]; }
+    for (int64_t tile = wglob; tile * 16 < N; tile += nw) {
+        const int64_t r0 = tile * 16 + g, r1 = r0 + 8;
+        float acc[8][4];
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) {
+            acc[nt][0] = acc[nt][2] = bias[nt][0];
+            acc[nt][1] = acc[nt][3] = bias[nt][1];
+        }
+#pragma unroll
+        for (int ks = 0; ks < K / 16; ++ks) {
+            const float *src = ks * 16 < DIN ? X : AGG;     // a k-step never straddles the two
+            const int kk = (ks * 16) % DIN + 2 * q;
+            const float2 z = make_float2(0.f, 0.f);
+            const float2 v00 = r0 < N ? *reinterpret_cast<const float2 *>(src + r0 * DIN + kk) : z;
+            const float2 v10 = r1 < N ? *reinterpret_cast<const float2 *>(src + r1 * DIN + kk) : z;
+            const float2 v01 = r0 < N ? *reinterpret_cast<const float2 *>(src + r0 * DIN + kk + 8) : z;
+            const float2 v11 = r1 < N ? *reinterpret_cast<const float2 *>(src + r1 * DIN + kk + 8) : z;
+            uint32_t ah[4], al[4];
+            split_bf16x2(v00.x, v00.y, ah[0], al[0]);
+            split_bf16x2(v10.x, v10.y, ah[1], al[1]);
+            split_bf16x2(v01.x, v01.y, ah[2], al[2]);
+            split_bf16x2(v11.x, v11.y, ah[3], al[3]);
+#pragma unroll
+            for (int nt = 0; nt < 8; ++nt) {
+                const uint32_t *wr = wt + (nt * 8 + g) * KP + ks * 8 + q;
+                const uint32_t b0 = wr[0], b1 = wr[4];
+                mma_bf16_16816(acc[nt], ah, b0, b1);
+                mma_bf16_16816(acc[nt], al, b0, b1);
+            }
+        }
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) {
+            const int c = nt * 8 + 2 * q;
+            if (r0 < N) *reinterpret_cast<float2 *>(H + r0 * HID + c) = make_float2(fmaxf(acc[nt][0], 0.f), fmaxf(acc[nt][1], 0.f));
+            if (r1 < N) *reinterpret_cast<float2 *>(H + r1 * HID + c) = make_float2(fmaxf(acc[nt][2], 0.f), fmaxf(acc[nt][3], 0.f));
+        }
+    }
+}
+
+// Backward (data) of one layer: dPRE = dH * [H > 0] (written out), then dXs = dPRE Ws^T and
+// T = dPRE Wn^T: K = 64, DIN outputs each, one pass per weight matrix.
+template <int DIN>
+__global__ void __launch_bounds__(256) dense_bwd_mma_kernel(int64_t N, const uint16_t *Ws, const uint16_t *Wn,
+                                                            const float *H, const float *dH, float *dPRE,
+                                                            float *dXs, float *T)
+{
+    constexpr int KP = HID / 2 + 4;
+    __shared__ uint32_t wt[2][DIN * KP];                  // [m][j][c pair]: W_m[j][c], W_m[j][c+1]
+    for (int t = threadIdx.x; t < DIN * (HID / 2); t += blockDim.x) {
+        const int j = t / (HID / 2), cp = t % (HID / 2);
+        wt[0][j * KP + cp] = reinterpret_cast<const uint32_t *>(Ws)[t];
+        wt[1][j * KP + cp] = reinterpret_cast<const uint32_t *>(Wn)[t];
+    }
+    __syncthreads();
+    constexpr int NT = DIN / 8;
+    const int lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
+    const int64_t wglob = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t tile = wglob; tile * 16 < N; tile += nw) {
+        const int64_t r0 = tile * 16 + g, r1 = r0 + 8;
+        // A fragments of dPRE for the 4 k-steps (c = 16 ks + ...), hi and lo parts
+        uint32_t ah[4][4], al[4][4];
+#pragma unroll
+        for (int ks = 0; ks < 4; ++ks) {
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                const int64_t r = (h & 1) ? r1 : r0;
+                const int c = ks * 16 + 2 * q + ((h & 2) ? 8 : 0);
+                float2 p = make_float2(0.f, 0.f);
+                if (r < N) {
+                    const float2 hv = *reinterpret_cast<const float2 *>(H + r * HID + c);
+                    const float2 dv = *reinterpret_cast<const float2 *>(dH + r * HID + c);
+                    p = make_float2(hv.x > 0.f ? dv.x : 0.f, hv.y > 0.f ? dv.y : 0.f);
+                    *reinterpret_cast<float2 *>(dPRE + r * HID + c) = p;
+                }
+                split_bf16x2(p.x, p.y, ah[ks][h], al[ks][h]);
+            }
+        }
+#pragma unroll
+        for (int m = 0; m < 2; ++m) {
+            float *out = m == 0 ? dXs : T;
+#pragma unroll
+            for (int nt = 0; nt < NT; ++nt) {
+                float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                for (int ks = 0; ks < 4; ++ks) {
+                    const uint32_t *wr = wt[m] + (nt * 8 + g) * KP + ks * 8 + q;
+                    const uint32_t b0 = wr[0], b1 = wr[4];
+                    mma_bf16_16816(acc, ah[ks], b0, b1);
+                    mma_bf16_16816(acc, al[ks], b0, b1);
+                }
+                const int j = nt * 8 + 2 * q;
+                if (r0 < N) *reinterpret_cast<float2 *>(out + r0 * DIN + j) = make_float2(acc[0], acc[1]);
+                if (r1 < N) *reinterpret_cast<float2 *>(out + r1 * DIN + j) = make_float2(acc[2], acc[3]);
+            }
+        }
     }
 }
 
@@ -285,15 +437,18 @@ __global__ void feat_init_kernel(int64_t N, int G, const int64_t *graph_ptr, con
     }
 }
 
-// per graph (one block): centre and scale channels of R, write X (N x 16) with degree features
+// per graph (one block): centre and scale channels of R, write X (N x 16) with degree features.
+// flags & GDI_MPNN_ALIGN: channel c >= 1 is multiplied by the sign of its inner product with
+// channel 0 (after centring), so that the channels' low-frequency components point the same way
+// inside a graph; flags & GDI_MPNN_NO_NOISE: the noise channels are written as 0.
 __global__ void feat_finish_kernel(int G, const int64_t *graph_ptr, const int64_t *row_ptr, const float *R,
-                                   float *X)
+                                   float *X, int flags)
 {
     const int g = blockIdx.x;
     const int64_t v0 = graph_ptr[g], v1 = graph_ptr[g + 1];
     const float n = (float)(v1 - v0);
     __shared__ float red[NRAND + 1][32];
-    __shared__ float mean[NRAND + 1], rms[NRAND];
+    __shared__ float mean[NRAND + 1], rms[NRAND], sgn[NRAND];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     float s[NRAND + 1];
 #pragma unroll
@@ -336,10 +491,33 @@ __global__ void feat_finish_kernel(int G, const int64_t *graph_ptr, const int64_
         rms[threadIdx.x] = sqrtf(a / n) + 1e-12f;
     }
     __syncthreads();
+    // inner products of the centred channels with channel 0
+#pragma unroll
+    for (int c = 0; c < NRAND; ++c) s[c] = 0.f;
+    if (flags & GDI_MPNN_ALIGN)
+        for (int64_t i = v0 + threadIdx.x; i < v1; i += blockDim.x) {
+            const float x0 = R[i * NRAND] - mean[0];
+#pragma unroll
+            for (int c = 1; c < NRAND; ++c) s[c] += x0 * (R[i * NRAND + c] - mean[c]);
+        }
+    __syncthreads();
+#pragma unroll
+    for (int c = 1; c < NRAND; ++c) {
+        const float a = warp_sum(s[c]);
+        if (lane == 0) red[c][w] = a;
+    }
+    __syncthreads();
+    if (threadIdx.x < NRAND) {
+        float a = 0.f;
+        if (threadIdx.x > 0 && (flags & GDI_MPNN_ALIGN))
+            for (int q = 0; q < nwarp; ++q) a += red[threadIdx.x][q];
+        sgn[threadIdx.x] = (flags & GDI_MPNN_NO_NOISE) ? 0.f : (a < 0.f ? -1.f : 1.f);
+    }
+    __syncthreads();
     for (int64_t i = v0 + threadIdx.x; i < v1; i += blockDim.x) {
         const float deg = (float)(row_ptr[i + 1] - row_ptr[i]);
 #pragma unroll
-        for (int c = 0; c < NRAND; ++c) X[i * FIN + c] = (R[i * NRAND + c] - mean[c]) / rms[c];
+        for (int c = 0; c < NRAND; ++c) X[i * FIN + c] = sgn[c] * ((R[i * NRAND + c] - mean[c]) / rms[c]);
         X[i * FIN + NRAND] = log1pf(deg);
         X[i * FIN + NRAND + 1] = mean[NRAND] > 0.f ? deg / mean[NRAND] : 0.f;
 #pragma unroll
@@ -403,9 +581,10 @@ extern "C" {
 
 int gdi_mpnn_features(int64_t N, int32_t G, const int64_t *graph_ptr, const uint32_t *graph_id,
                       const int64_t *row_ptr, const int32_t *col, uint64_t seed, int32_t steps,
-                      float *X, float *scratch, void *stream)
+                      int32_t flags, float *X, float *scratch, void *stream)
 {
-    if (N < 1 || G < 1 || steps < 0 || !graph_ptr || !graph_id || !row_ptr || !col || !X || !scratch)
+    if (N < 1 || G < 1 || steps < 0 || !graph_ptr || !graph_id || !row_ptr || !col || !X || !scratch ||
+        (flags & ~(GDI_MPNN_ALIGN | GDI_MPNN_NO_NOISE)))
         return GDI_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     float *R0 = scratch, *R1 = scratch + N * NRAND;
@@ -415,7 +594,7 @@ int gdi_mpnn_features(int64_t N, int32_t G, const int64_t *graph_ptr, const uint
         aggregate_kernel<<<grid_for(N * 32, 256), 256, 0, st>>>(N, row_ptr, col, R0, NRAND, R1, 2, 0);
         float *t = R0; R0 = R1; R1 = t;
     }
-    feat_finish_kernel<<<G, 256, 0, st>>>(G, graph_ptr, row_ptr, R0, X);
+    feat_finish_kernel<<<G, 256, 0, st>>>(G, graph_ptr, row_ptr, R0, X, flags);
     return cudaGetLastError() == cudaSuccess ? GDI_OK : GDI_ERR_CUDA;
 }
 
@@ -432,8 +611,18 @@ int gdi_mpnn_dense_fwd(int64_t N, const float *X, const float *AGG, int32_t din,
                        const uint16_t *Wn, const float *b, float *H, void *stream)
 {
     if (N < 1 || din < 1 || din > 64) return GDI_ERR_INVALID_ARG;
-    const size_t smem = 2 * (size_t)din * HID * sizeof(float);
-    dense_fwd_kernel<<<grid_for(N * 32, 256), 256, smem, (cudaStream_t)stream>>>(N, X, AGG, din, Ws, Wn, b, H, 1);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int tb = (int)min((N + 15) / 16 * 32 / 256 + 1, (int64_t)152 * 16);   // tiles of 16 rows, 8 warps a block
+    // the tensor-core kernels move activations in pairs (8-byte accesses)
+    const bool pairs = aligned(X, 8) && aligned(AGG, 8) && aligned(H, 8);
+    if (din == 64 && pairs) {
+        dense_fwd_mma_kernel<64><<<tb, 256, 0, st>>>(N, X, AGG, Ws, Wn, b, H);
+    } else if (din == 16 && pairs) {
+        dense_fwd_mma_kernel<16><<<tb, 256, 0, st>>>(N, X, AGG, Ws, Wn, b, H);
+    } else {
+        const size_t smem = 2 * (size_t)din * HID * sizeof(float);
+        dense_fwd_kernel<<<grid_for(N * 32, 256), 256, smem, st>>>(N, X, AGG, din, Ws, Wn, b, H, 1);
+    }
     return cudaGetLastError() == cudaSuccess ? GDI_OK : GDI_ERR_CUDA;
 }
 
@@ -441,8 +630,19 @@ int gdi_mpnn_dense_bwd(int64_t N, int32_t din, const uint16_t *Ws, const uint16_
                        const float *dH, float *dPRE, float *dXs, float *T, void *stream)
 {
     if (N < 1 || din < 1 || din > 64) return GDI_ERR_INVALID_ARG;
-    const size_t smem = 2 * (size_t)din * HID * sizeof(float);
-    dense_bwd_kernel<<<grid_for(N * 32, 256), 256, smem, (cudaStream_t)stream>>>(N, din, Ws, Wn, H, dH, dPRE, dXs, T);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int tb = (int)min((N + 15) / 16 * 32 / 256 + 1, (int64_t)152 * 16);
+    // pairs of activations (8-byte accesses) and pairs of BF16 weights (4-byte accesses)
+    const bool pairs = aligned(H, 8) && aligned(dH, 8) && aligned(dPRE, 8) && aligned(dXs, 8) && aligned(T, 8) &&
+                       aligned(Ws, 4) && aligned(Wn, 4);
+    if (din == 64 && pairs) {
+        dense_bwd_mma_kernel<64><<<tb, 256, 0, st>>>(N, Ws, Wn, H, dH, dPRE, dXs, T);
+    } else if (din == 16 && pairs) {
+        dense_bwd_mma_kernel<16><<<tb, 256, 0, st>>>(N, Ws, Wn, H, dH, dPRE, dXs, T);
+    } else {
+        const size_t smem = 2 * (size_t)din * HID * sizeof(float);
+        dense_bwd_kernel<<<grid_for(N * 32, 256), 256, smem, st>>>(N, din, Ws, Wn, H, dH, dPRE, dXs, T);
+    }
     return cudaGetLastError() == cudaSuccess ? GDI_OK : GDI_ERR_CUDA;
 }
 

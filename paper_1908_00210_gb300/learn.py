@@ -38,7 +38,7 @@ def lib():
     if _L is None:
         L = B.load()
         vp, i32, i64, f32, u64 = C.c_void_p, C.c_int32, C.c_int64, C.c_float, C.c_uint64
-        L.gdi_mpnn_features.argtypes = [i64, i32, vp, vp, vp, vp, u64, i32, vp, vp, vp]
+        L.gdi_mpnn_features.argtypes = [i64, i32, vp, vp, vp, vp, u64, i32, i32, vp, vp, vp]
         L.gdi_mpnn_aggregate.argtypes = [i64, vp, vp, vp, i32, vp, i32, i32, vp]
         L.gdi_mpnn_dense_fwd.argtypes = [i64, vp, vp, i32, vp, vp, vp, vp, vp]
         L.gdi_mpnn_dense_bwd.argtypes = [i64, i32, vp, vp, vp, vp, vp, vp, vp, vp]
@@ -116,7 +116,7 @@ class MPNN:
     """Parameters, optimiser state and activation buffers of the network on the device."""
 
     def __init__(self, params: np.ndarray | None = None, seed: int = 0, lr: float = 1e-3,
-                 lam: float = 0.1, feat_seed: int = 0x9E3779B9, steps: int = 256):
+                 lam: float = 0.1, feat_seed: int = 0x9E3779B9, steps: int = 256, feat_flags: int = 0):
         import torch
         self.torch = torch
         off, total = param_layout()
@@ -129,6 +129,7 @@ class MPNN:
         self.v = torch.zeros_like(self.grads)
         self.step = 0
         self.lr, self.lam, self.feat_seed, self.steps = lr, lam, feat_seed, steps
+        self.feat_flags = feat_flags          # GDI_MPNN_ALIGN | GDI_MPNN_NO_NOISE
         _ok(lib().gdi_mpnn_to_bf16(total, self.params.data_ptr(), self.params_bf16.data_ptr(), self._st()), "to_bf16")
 
     def _st(self):
@@ -149,7 +150,8 @@ class MPNN:
         X = t.empty((b.N, FIN), dtype=t.float32, device="cuda")
         scratch = t.empty((2 * b.N * 8,), dtype=t.float32, device="cuda")
         _ok(lib().gdi_mpnn_features(b.N, b.G, b.graph_ptr.data_ptr(), b.graph_id.data_ptr(), b.row_ptr.data_ptr(),
-                                    b.col.data_ptr(), self.feat_seed, self.steps, X.data_ptr(), scratch.data_ptr(),
+                                    b.col.data_ptr(), self.feat_seed, self.steps, self.feat_flags, X.data_ptr(),
+                                    scratch.data_ptr(),
                                     self._st()), "features")
         return X
 
@@ -340,13 +342,16 @@ def anneal_batch(graphs, *, sweeps, t0, t1, seed, replicas, init=None, A=1, Bc=4
     return cut, spins, ms
 
 
-def label_graphs(graphs, *, sweeps=2000, replicas=4, seed=1, chunk=2048, A=1):
-    """Labels = the best (lowest repaired cut) of `replicas` plain random-start anneals, annealed
-    `chunk` graphs per batched launch."""
+def label_graphs(graphs, *, sweeps=2000, replicas=4, seed=1, chunk=2048, A=1, start=None, t0=3.0):
+    """Labels = the best (lowest repaired cut) of `replicas` anneals, annealed `chunk` graphs per
+    batched launch: plain random-start anneals from T = t0, or (start = a function of a list of
+    graphs returning exactly balanced device spins) anneals from that start."""
     ys, bests = [], []
     for g0 in range(0, len(graphs), chunk):
         part = graphs[g0:g0 + chunk]
-        cut, spins, _ = anneal_batch(part, sweeps=sweeps, t0=3.0, t1=0.05, seed=seed, replicas=replicas, A=A)
+        init = None if start is None else start(part).repeat(replicas)
+        cut, spins, _ = anneal_batch(part, sweeps=sweeps, t0=t0, t1=0.05, seed=seed, replicas=replicas, A=A,
+                                     init=init)
         from gdi_synth import batch_union
         gp, _ = batch_union(part)
         y = np.empty(gp[-1], dtype=np.int8)
@@ -447,9 +452,13 @@ def evaluate_many(starts, graphs, *, seeds=8, full_sweeps=2000, ladder=LADDER, A
     out = {"c_ref_median": float(np.median(c_ref)), "full_random_ms": full_ms, "graphs": len(graphs),
            "seeds": seeds, "ladder": ladder, "A": A}
     methods = {"random_T3.0": dict(t0=3.0, init=None, infer=0.0)}
-    for t_low in sorted({t for _, t in starts.values()}):
+    for t_low in sorted({st[-2] if st[0] == "spins" and len(st) > 3 else st[-1] for st in starts.values()}):
         methods[f"random_T{t_low}"] = dict(t0=t_low, init=None, infer=0.0)
-    for name, (model, t_low) in starts.items():
+    for name, st in starts.items():
+        if st[0] == "spins":                         # a start given as spins (already computed)
+            methods[name] = dict(t0=st[2], init=st[1].repeat(seeds), infer=st[3] if len(st) > 3 else 0.0)
+            continue
+        model, t_low = st
         gb = GraphBatch.from_graphs(graphs, graph_ids=np.arange(len(graphs)) + 1_000_000)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -517,6 +526,63 @@ def ablate(args, log):
     return res
 
 
+def channel_spins(model: "MPNN", graphs, channel: int = 0):
+    """Exactly balanced spins from one input feature channel alone (the diffused noise channel 0 is a
+    cheap spectral embedding): the same rounding as the network's logits, applied to X[:, channel]."""
+    import torch
+    gb = GraphBatch.from_graphs(graphs, graph_ids=np.arange(len(graphs)) + 1_000_000)
+    X = model.features(gb)
+    z = X[:, channel].contiguous()
+    s = torch.empty((gb.N,), dtype=torch.int8, device="cuda")
+    _ok(lib().gdi_mpnn_round(gb.G, gb.graph_ptr.data_ptr(), gb.max_n, z.data_ptr(), s.data_ptr(), model._st()), "round")
+    return s
+
+
+def ablate_starts(args, log):
+    """What the trained network adds: one set of graphs and labels; the held-out graphs annealed
+    from (1) the rounded diffused noise channel 0 alone, (2) an untrained network, (3) a network
+    trained without the noise channels, (4) the trained network, next to the plain annealer and the
+    random start at the same low temperature.  Features sign-aligned per graph (GDI_MPNN_ALIGN)
+    unless --no-align."""
+    import torch
+    t0 = time.time()
+    train_graphs = make_graphs_parallel(args.train, 500_000, processes=args.processes)
+    test_graphs = make_graphs_parallel(args.test, 900_000, processes=args.processes)
+    log(f"graphs generated in {time.time() - t0:.1f} s")
+    torch.cuda.set_device(0)
+    t0 = time.time()
+    flags = 0 if args.no_align else 1
+    if args.label_start == "spectral":
+        # labels refined from the network's own spectral input: the rounded noise channel 0,
+        # annealed from T0 = t_low -- a target that is one good partition the features point to
+        probe = MPNN(seed=0, steps=args.steps, feat_flags=flags)
+        labels, _ = label_graphs(train_graphs, sweeps=args.label_sweeps, A=args.A, t0=args.t_low,
+                                 start=lambda part: channel_spins(probe, part, 0))
+    else:
+        labels, _ = label_graphs(train_graphs, sweeps=args.label_sweeps, A=args.A)
+    log(f"labels ({args.label_start} start) in {time.time() - t0:.1f} s")
+    nets, losses = {}, {}
+    for name, fl in (("trained", flags), ("trained_no_noise", flags | 2)):
+        model = MPNN(seed=0, lr=args.lr, lam=args.lam, steps=args.steps, feat_flags=fl)
+        ds = Dataset(train_graphs, labels, model)
+        t0 = time.time()
+        losses[name] = train_dataset(model, ds, epochs=args.epochs, log=log)
+        log(f"{name}: trained in {time.time() - t0:.1f} s, loss {losses[name][0]:.4f} -> {losses[name][-1]:.4f}")
+        del ds
+        nets[name] = model
+    untrained = MPNN(seed=0, lr=args.lr, lam=args.lam, steps=args.steps, feat_flags=flags)
+    t = args.t_low
+    starts = {"noise_channel0": ("spins", channel_spins(untrained, test_graphs, 0), t),
+              "untrained": (untrained, t), "trained_no_noise": (nets["trained_no_noise"], t),
+              "trained": (nets["trained"], t)}
+    res = evaluate_many(starts, test_graphs, A=args.A, log=log)
+    res["train_loss"] = losses
+    res["train_graphs"] = args.train
+    res["feature_flags"] = flags
+    res["label_start"] = args.label_start
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--train", type=int, default=1024)
@@ -532,8 +598,22 @@ def main():
     ap.add_argument("--A", type=int, default=1, help="balance weight of the anneals (labels and evaluation)")
     ap.add_argument("--ablate-steps", default="", help="comma list of diffusion steps: ablation mode")
     ap.add_argument("--ablate-t", default="0.5", help="comma list of start temperatures (ablation mode)")
+    ap.add_argument("--ablate-starts", action="store_true",
+                    help="compare the trained network with the noise channel alone, an untrained network "
+                         "and a network trained without the noise channels")
+    ap.add_argument("--no-align", action="store_true", help="features without the per-graph sign alignment")
+    ap.add_argument("--label-start", default="random", choices=["random", "spectral"],
+                    help="training labels from random-start anneals (T0 = 3.0) or from anneals that start at "
+                         "the rounded noise channel 0 (T0 = --t-low) (--ablate-starts)")
     args = ap.parse_args()
     log = lambda s: print(s, flush=True)  # noqa: E731
+    if args.ablate_starts:
+        res = ablate_starts(args, log)
+        print(json.dumps({k: v for k, v in res.items() if k != "train_loss"}, default=str))
+        if args.out:
+            with open(args.out, "w") as f:
+                json.dump(res, f, default=str, indent=1)
+        return
     if args.ablate_steps:
         res = ablate(args, log)
         print(json.dumps({k: v for k, v in res.items() if k != "train_loss"}, default=str))

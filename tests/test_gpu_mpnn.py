@@ -25,10 +25,12 @@ def setup(gdi):
     return learn, torch, gs, ids, b, gp, u, y, model
 
 
-def test_features_match_oracle(setup):
+@pytest.mark.parametrize("flags", [0, 1, 3])
+def test_features_match_oracle(setup, flags):
     learn, torch, gs, ids, b, gp, u, y, model = setup
-    X = model.features(b).cpu().numpy()
-    Xr = ref.features(gp, ids, u.row_ptr, u.col, 12345, 3)
+    m = learn.MPNN(seed=3, lam=0.2, feat_seed=12345, steps=3, feat_flags=flags)
+    X = m.features(b).cpu().numpy()
+    Xr = ref.features(gp, ids, u.row_ptr, u.col, 12345, 3, flags)
     assert np.max(np.abs(X - Xr)) < 1e-4
 
 
@@ -122,9 +124,9 @@ def test_shipped_settings_features_logits_gradients_vs_fp64(gdi):
     ids = np.arange(900000, 900016, dtype=np.uint32)
     b = learn.GraphBatch.from_graphs(gs, graph_ids=ids)
     gp, u = batch_union(gs)
-    model = learn.MPNN(seed=21, lam=0.1, feat_seed=0x9E3779B9, steps=256)
+    model = learn.MPNN(seed=21, lam=0.1, feat_seed=0x9E3779B9, steps=256, feat_flags=1)
     X = model.features(b)
-    Xr = ref.features(gp, ids, u.row_ptr, u.col, 0x9E3779B9, 256)
+    Xr = ref.features(gp, ids, u.row_ptr, u.col, 0x9E3779B9, 256, ref.ALIGN)
     ferr = np.max(np.abs(X.cpu().numpy() - Xr))
     assert ferr < 1e-3, ferr
     z, cache = model.forward(b, X)

@@ -150,3 +150,29 @@ def test_user_init_spins(gdi):
     init = np.where(rng.random((2, g.n)) < 0.5, 1, -1).astype(np.int8)
     out = run_both(gdi, g, A=1, B=4, W=64, sweeps=30, t0=12.0, t1=0.2, seed=6, replicas=2, init=init)
     assert_parity(*out)
+
+
+@pytest.mark.parametrize("W,mode,A", [(64, 0, 1), (1, 0, 1), (0, 1, 2), (16, 1, 1)])
+def test_standard_mode_matches_stale_oracle(gdi, W, mode, A):
+    """Algorithm 2 (GDI_FLAG_STANDARD): every spin reads all n spins for the balance term and the
+    spins of a window decide on the window-start state; bit-exact to the oracle's stale reading,
+    in both table modes, for one spin per window and for whole classes."""
+    g = erdos_renyi(700, 0.03, 77, signed=True)
+    ann = gdi.Annealer(g, A=A, B=4, W=W, replicas=3)
+    ann.configure(path=gdi.GDI_PATH_CTA)
+    sch = gdi.Schedule(sweeps=60, t0=12.0, t1=0.2, mode=mode, pf0=0.2, pf1=0.001)
+    ann.anneal(sch, 9, flags=gdi.GDI_FLAG_TRACE | gdi.GDI_FLAG_STANDARD)
+    res, spins, tr = ann.results(), ann.spins(), ann.trace()
+    ann.close()
+    ref = oracle.anneal(g, A=A, B=4, W=W, mode=mode, t0=12.0, t1=0.2, pf0=0.2, pf1=0.001, sweeps=60,
+                        seed=9, replicas=3, stale=True)
+    assert_parity(res, spins, tr, ref)
+
+
+def test_standard_mode_rejected_on_grid_path(gdi):
+    g = erdos_renyi(300, 0.05, 78)
+    ann = gdi.Annealer(g, A=1, B=4, W=16, replicas=1)
+    ann.configure(path=gdi.GDI_PATH_GRID)
+    with pytest.raises(gdi.GdiError):
+        ann.anneal(gdi.Schedule(sweeps=4), 1, flags=gdi.GDI_FLAG_STANDARD)
+    ann.close()

@@ -242,3 +242,21 @@ def test_loss_closed_form_for_constant_logits(c, lam):
     z = np.full(14, c)
     L, _, _ = mpnn.loss(gp, z, y, lam)
     assert L == pytest.approx(np.log(2 * np.cosh(c / 2)) + lam * np.tanh(c) ** 2, rel=1e-12)
+
+
+def test_feature_alignment_and_noise_mask():
+    """ALIGN flips whole noise channels so that each has a non-negative inner product with channel 0
+    inside every graph (and changes nothing else); NO_NOISE zeroes the noise channels only."""
+    gs, gp, u = _batch()
+    ids = np.array([3, 4, 5], dtype=np.uint32)
+    X0 = mpnn.features(gp, ids, u.row_ptr, u.col, 21, 6)
+    Xa = mpnn.features(gp, ids, u.row_ptr, u.col, 21, 6, mpnn.ALIGN)
+    Xn = mpnn.features(gp, ids, u.row_ptr, u.col, 21, 6, mpnn.NO_NOISE)
+    assert np.array_equal(np.abs(Xa), np.abs(X0)) and np.array_equal(Xa[:, 8:], X0[:, 8:])
+    for g in range(len(gs)):
+        s = slice(gp[g], gp[g + 1])
+        dots = Xa[s, :8].T @ Xa[s, 0]
+        assert np.all(dots >= 0)
+        for c in range(8):                       # each channel is the unaligned one or its negative
+            assert np.array_equal(Xa[s, c], X0[s, c]) or np.array_equal(Xa[s, c], -X0[s, c])
+    assert np.all(Xn[:, :8] == 0) and np.array_equal(Xn[:, 8:], X0[:, 8:])

@@ -400,3 +400,31 @@ def test_replica_offset_selects_the_same_streams():
     b = oracle.anneal(g, A=1, B=4, W=16, sweeps=20, t0=12.0, t1=0.2, seed=5, replicas=2, first_replica=2)
     assert np.array_equal(a.spins[2:], b.spins) and np.array_equal(a.digest[2:], b.digest)
     assert np.array_equal(a.final_cut[2:], b.final_cut) and np.array_equal(a.G_trace[2:], b.G_trace)
+
+
+@pytest.mark.parametrize("mode", [oracle.METROPOLIS, oracle.PAPER_PF])
+def test_stale_reading_special_cases(mode):
+    """The stale reading (every spin of a window sees the G of the window start): with one spin per
+    window (W = 1) it is the running-G method itself, and with A = 0 no decision depends on G, so it
+    equals the method for any W; tracked G and cut stay exact."""
+    g = barabasi_albert(400, 3, 31)
+    kw = dict(B=4, t0=12.0, t1=0.2, pf0=0.2, pf1=0.005, sweeps=25, seed=7, replicas=2, mode=mode)
+    a = oracle.anneal(g, A=1, W=1, **kw)
+    b = oracle.anneal(g, A=1, W=1, stale=True, **kw)
+    assert np.array_equal(a.spins, b.spins) and np.array_equal(a.digest, b.digest)
+    a = oracle.anneal(g, A=0, W=0, **kw)
+    b = oracle.anneal(g, A=0, W=0, stale=True, **kw)
+    assert np.array_equal(a.spins, b.spins) and np.array_equal(a.digest, b.digest)
+    c = oracle.anneal(g, A=1, W=0, stale=True, check_invariants=True, **kw)
+    assert c.invariant_failures == 0
+
+
+def test_stale_reading_overshoots_by_hand():
+    """Hand case: 4 isolated vertices all +1 (G = 4), A = 1, B = 1, one window, zero temperature.
+    Running G: spins flip while dE = 4A(1 - G) <= 0, i.e. while G >= 1: 4 -> 2 -> 0, then stop (two
+    flips, G = 0).  Stale G = 4: every spin sees dE = -12 and flips, G = -4 (the overshoot)."""
+    g = from_edges(4, np.array([], dtype=np.int64), np.array([], dtype=np.int64))
+    init = np.ones((1, 4), dtype=np.int8)
+    kw = dict(A=1, B=1, W=0, t0=1e-3, t1=1e-3, sweeps=1, seed=3, init=init, repair=False)
+    assert oracle.anneal(g, **kw).raw_G[0] == 0
+    assert oracle.anneal(g, stale=True, **kw).raw_G[0] == -4
