@@ -764,6 +764,7 @@ int gdi_anneal(gdi_ctx *c, const gdi_schedule *S, const gdi_run *run)
     }
     if (!grid) {
         cudaMemsetAsync(c->item_counter.p, 0, sizeof(int32_t), st);
+        cudaMemsetAsync(c->err.p, 0, sizeof(int32_t), st);
         if (need > (size_t)max_optin)
             return fail(GDI_ERR_TOO_LARGE, "instance needs " + std::to_string(need) +
                                                " bytes of shared memory per block (limit " +
@@ -849,6 +850,11 @@ static int sync_ctx(gdi_ctx *c)
         e = cudaMemcpy(&err, c->g_err.p, sizeof(int32_t), cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) return cuda_fail(e, "error word");
         if (err == GDI_DEVERR_TIMEOUT) return fail(GDI_ERR_TIMEOUT, "a grid barrier wait ran out");
+        if (err) return fail(GDI_ERR_CUDA, "device error word " + std::to_string(err));
+    } else {
+        int32_t err = 0;
+        e = cudaMemcpy(&err, c->err.p, sizeof(int32_t), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(e, "error word");
         if (err) return fail(GDI_ERR_CUDA, "device error word " + std::to_string(err));
     }
     return GDI_OK;

@@ -28,10 +28,12 @@
 
 #include "gdi_device.cuh"
 #include "gdi_internal.h"
+#include "gdi_window.cuh"
 
 namespace {
 
 using namespace gdi;
+using namespace gdi::win;
 
 // ---------------------------------------------------------------------------------------------
 struct Smem {
@@ -393,6 +395,212 @@ __global__ void __launch_bounds__(BS) gdi_cta_anneal_kernel(GdiDevProblem P, Gdi
     }
 }
 
+// ---------------------------------------------------------------------------------------------
+// CTA-resident sorted-window kernel (1 <= W <= 256): the same results as gdi_cta_anneal_kernel with
+// far fewer block barriers per window.  Per colour class: every thread computes the thresholds of
+// its ranks of the class (fields gathered from the shared spins); every warp sorts whole windows
+// of the class (window_maps: one comparison value per member, valid for any G entering the window,
+// gdi_window.cuh); then one warp replays the windows in rank order from the class-start G -- each
+// window two rounds of ballots -- and the flips are applied.  The windows of a class share no edge,
+// so only the running G passes from one window to the next.  SL = members per lane of a window.
+struct SortedCta {
+    int32_t *gam;       // [max_class] flip thresholds of the class
+    int16_t *rel;       // [max_class] comparison values
+    uint8_t *s0;        // [max_class] 1 = the member was -1 at window start
+    uint8_t *narrow;    // [windows of the largest class] window sorted with 16-bit keys
+    uint32_t *fbits;    // [max_class / 32 + 2] flips of the fast replay
+    uint32_t *fm;       // [max_class / 4 + 2] flips of the exact replay (byte per member)
+    int32_t *bins;      // [HA] exact-replay histogram
+    StageMap *maps;     // [warps][2] stage maps (only the narrow flag is used here)
+};
+
+__host__ __device__ inline size_t align16c(size_t x) { return (x + 15) & ~(size_t)15; }
+
+// Shared-memory layout of the sorted CTA kernel, one function for the kernel's carving and the
+// host's size: the common part (reductions, G, table row, spins, repair flags), then the class
+// buffers.  Every array starts on a 16-byte boundary.
+struct CtaSortedLayout {
+    size_t red64, red32, G, row, sig, flag, gam, rel, s0, narrow, fbits, fm, bins, maps, total;
+};
+
+__host__ __device__ inline CtaSortedLayout cta_sorted_layout(int32_t max_n, int32_t max_class, int32_t max_row,
+                                                             int W, int BS)
+{
+    CtaSortedLayout L;
+    const size_t mc = (size_t)max_class + 8;
+    size_t o = 0;
+    L.red64 = o; o = align16c(o + sizeof(int64_t) * (BS / 32 + 2));
+    L.red32 = o; o = align16c(o + sizeof(int32_t) * (BS / 32 + 2));
+    L.G = o; o = align16c(o + 16);
+    L.row = o; o = align16c(o + sizeof(uint32_t) * (size_t)(max_row + 4));
+    L.sig = o; o = align16c(o + (size_t)max_n + 16);
+    L.flag = o; o = align16c(o + (size_t)max_n + 16);
+    L.gam = o; o = align16c(o + 4 * mc);
+    L.rel = o; o = align16c(o + 2 * mc);
+    L.s0 = o; o = align16c(o + mc);
+    L.narrow = o; o = align16c(o + (size_t)((max_class + W - 1) / W) + 4);
+    L.fbits = o; o = align16c(o + 4 * (mc / 32 + 2));
+    L.fm = o; o = align16c(o + 4 * (mc / 4 + 2));
+    L.bins = o; o = align16c(o + 4 * (size_t)win::HA);
+    L.maps = o; o = align16c(o + sizeof(StageMap) * 2 * (size_t)(BS / 32));
+    L.total = o;
+    return L;
+}
+
+__host__ __device__ inline size_t cta_sorted_smem(int32_t max_n, int32_t max_class, int32_t max_row, int W, int BS)
+{
+    return cta_sorted_layout(max_n, max_class, max_row, W, BS).total;
+}
+
+template <int BS, int SL>
+__global__ void __launch_bounds__(BS) gdi_cta_sorted_kernel(GdiDevProblem P, GdiDevRun R)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Smem S = {};
+    SortedCta C;
+    {
+        const CtaSortedLayout L = cta_sorted_layout(P.max_n, P.max_class, R.max_row, P.W, BS);
+        S.red64 = reinterpret_cast<int64_t *>(smem_raw + L.red64);
+        S.red32 = reinterpret_cast<int32_t *>(smem_raw + L.red32);
+        S.G = reinterpret_cast<int32_t *>(smem_raw + L.G);
+        S.row = reinterpret_cast<uint32_t *>(smem_raw + L.row);
+        S.sig = reinterpret_cast<int8_t *>(smem_raw + L.sig);
+        S.flag = reinterpret_cast<int8_t *>(smem_raw + L.flag);
+        C.gam = reinterpret_cast<int32_t *>(smem_raw + L.gam);
+        C.rel = reinterpret_cast<int16_t *>(smem_raw + L.rel);
+        C.s0 = smem_raw + L.s0;
+        C.narrow = smem_raw + L.narrow;
+        C.fbits = reinterpret_cast<uint32_t *>(smem_raw + L.fbits);
+        C.fm = reinterpret_cast<uint32_t *>(smem_raw + L.fm);
+        C.bins = reinterpret_cast<int32_t *>(smem_raw + L.bins);
+        C.maps = reinterpret_cast<StageMap *>(smem_raw + L.maps);
+        // the launch must have given the whole layout (the host sizes it with the same function)
+        uint32_t dyn;
+        asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
+        if ((size_t)dyn < L.total) {
+            if (threadIdx.x == 0 && blockIdx.x == 0) atomicCAS(R.err, 0, GDI_DEVERR_INPUT);
+            return;
+        }
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int W = P.W;
+    const int32_t items = P.num_instances * P.replicas;
+    __shared__ int32_t next_item;
+    while (true) {
+        __syncthreads();
+        if (threadIdx.x == 0) next_item = atomicAdd(R.item_counter, 1);
+        __syncthreads();
+        const int32_t slot = next_item;
+        if (slot >= items) break;
+        const int32_t item = R.item_order[slot];
+        const int32_t q = item / P.replicas;
+        const int32_t rep = item - q * P.replicas;
+        const int64_t base = P.node_off[q];
+        const int32_t n = (int32_t)(P.node_off[q + 1] - base);
+        const int32_t *cls = P.class_ptr + P.class_off[q];
+        const int32_t ncls = P.class_off[q + 1] - P.class_off[q] - 1;
+        int8_t *gsig = R.spins + (int64_t)rep * P.N + base;
+
+        int32_t g = 0;
+        for (int32_t r = threadIdx.x; r < n; r += BS) {
+            const int8_t sv = gsig[r];
+            S.sig[r] = sv;
+            g += sv;
+        }
+        g = block_sum<BS, int32_t>(g, S.red32);
+        if (threadIdx.x == 0) *S.G = g;
+        __syncthreads();
+
+        for (int32_t sw = R.s_begin; sw < R.s_end; ++sw) {
+            const int32_t roff = R.tab_off[sw];
+            const int32_t rlen = R.tab_off[sw + 1] - roff;
+            for (int32_t k = threadIdx.x; k < rlen; k += BS) S.row[k] = R.tab[roff + k];
+            const float Tsw = R.temp ? R.temp[sw] : 0.f;
+            const bool plus_first = (sw & 1) == 0;
+            __syncthreads();
+            for (int32_t c = 0; c < ncls; ++c) {
+                const int32_t lo = cls[c], hi = cls[c + 1];
+                const int32_t ns = hi - lo;
+                const int32_t nwin = (ns + W - 1) / W;
+                const int32_t c0 = *S.G;                 // G at class start (the reference c)
+                // thresholds of the class's ranks, one Philox call per aligned quad
+                for (int32_t qd = (lo >> 2) + threadIdx.x; qd <= ((hi - 1) >> 2); qd += BS) {
+                    const uint4 u4 = philox4x32_10(
+                        make_uint4((uint32_t)qd, (uint32_t)sw, (uint32_t)q, (uint32_t)rep), R.key0, R.key1);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const int32_t r = 4 * qd + j;
+                        if (r < lo || r >= hi) continue;
+                        const int sg = S.sig[r];
+                        const int32_t h = local_field(P, base, r, S.sig);
+                        const int32_t es = estar_of(S.row, rlen, R.mode, word_of(u4, j), Tsw);
+                        C.gam[r - lo] = gamma_of(sg, h, es, P.A, P.B);
+                        C.s0[r - lo] = sg < 0 ? 1 : 0;
+                    }
+                }
+                for (int32_t i = threadIdx.x; i < ns / 32 + 2; i += BS) C.fbits[i] = 0;
+                for (int32_t i = threadIdx.x; i < ns / 4 + 2; i += BS) C.fm[i] = 0;
+                __syncthreads();
+                // every window sorted by one warp
+                for (int32_t kk = warp; kk < nwin; kk += BS / 32) {
+                    const int32_t ws = kk * W, wlen = min(W, ns - ws);
+                    window_maps<SL>(C.gam, C.s0, C.rel, ws, wlen, 0, c0, C.maps + 2 * warp);
+                    __syncwarp();
+                    if (lane == 0) C.narrow[kk] = (uint8_t)C.maps[2 * warp].narrow;
+                }
+                __syncthreads();
+                // the windows in rank order, each entered with the G its predecessors left
+                if (warp == 0) {
+                    int32_t x = 0;
+                    for (int32_t kk = 0; kk < nwin; ++kk) {
+                        const int32_t ws = kk * W, we = min(ws + W, ns);
+                        const bool on = C.narrow[kk] ? (x >= -NT && x <= NT - 2) : (x >= -FAST_X && x <= FAST_X);
+                        x = on ? replay_window<SL>(C.rel, C.s0, 0, ws, we, x, plus_first, C.fbits, W)
+                               : window_replay_exact(C.gam, C.s0, 0, ws, we, c0 + x, plus_first, C.bins, C.fm) - c0;
+                    }
+                    if (lane == 0) *S.G = c0 + x;
+                }
+                __syncthreads();
+                for (int32_t i = threadIdx.x; i < ns; i += BS) {
+                    const uint32_t f = ((C.fbits[i >> 5] >> (i & 31)) | (C.fm[i >> 2] >> (8 * (i & 3)))) & 1u;
+                    if (f) S.sig[lo + i] = (int8_t)-S.sig[lo + i];
+                }
+                __syncthreads();
+            }
+            if (R.flags & GDI_DEV_TRACE) {
+                uint64_t dg = 0;
+                for (int32_t r = threadIdx.x; r < n; r += BS)
+                    if (S.sig[r] > 0)
+                        dg += splitmix64_fin((uint64_t)(uint32_t)r | ((uint64_t)(sw & 0xFFFF) << 32) |
+                                             ((uint64_t)(rep & 0xFFFF) << 48));
+                dg = block_sum<BS, uint64_t>(dg, reinterpret_cast<uint64_t *>(S.red64));
+                const int64_t ct = item_cut<BS>(P, base, n, S);
+                if (threadIdx.x == 0) {
+                    const int64_t o = (int64_t)item * R.sweeps + sw;
+                    R.tr_digest[o] = dg;
+                    R.tr_G[o] = *S.G;
+                    R.tr_cut[o] = ct;
+                }
+            }
+            __syncthreads();
+        }
+        const int64_t raw_cut = item_cut<BS>(P, base, n, S);
+        __syncthreads();
+        const int32_t raw_G = *S.G;
+        if (!(R.flags & GDI_DEV_NO_REPAIR)) repair<BS>(P, base, n, S);
+        const int64_t fin_cut = item_cut<BS>(P, base, n, S);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            R.raw_G[item] = raw_G;
+            R.raw_cut[item] = raw_cut;
+            R.final_G[item] = *S.G;
+            R.final_cut[item] = fin_cut;
+        }
+        for (int32_t r = threadIdx.x; r < n; r += BS) gsig[r] = S.sig[r];
+        __syncthreads();
+    }
+}
+
 // Initial state (Alg. 3 "initialize all s_i"): balanced random pairs from Philox, or the caller's
 // spins scattered from original order to rank order.
 __global__ void gdi_init_kernel(GdiDevProblem P, int8_t *spins, const int8_t *init_orig, int kind,
@@ -460,26 +668,55 @@ int hist_bins(const GdiDevProblem &P)
     return H;
 }
 
+// the sorted-window kernel serves every window size 1 .. 256 (one instantiation per members per
+// lane) of the running-G method; Algorithm 2 (GDI_DEV_STANDARD) stays on gdi_cta_anneal_kernel
+inline bool cta_sorted(const GdiDevProblem &P, const GdiDevRun &R)
+{
+    return P.W >= 1 && P.W <= 256 && !(R.flags & GDI_DEV_STANDARD);
+}
+
+template <int BS>
+const void *cta_kernel(const GdiDevProblem &P, const GdiDevRun &R)
+{
+    if (!cta_sorted(P, R)) return (const void *)gdi_cta_anneal_kernel<BS>;
+    return P.W <= 32 ? (const void *)gdi_cta_sorted_kernel<BS, 1>
+         : P.W <= 64 ? (const void *)gdi_cta_sorted_kernel<BS, 2>
+         : P.W <= 128 ? (const void *)gdi_cta_sorted_kernel<BS, 4>
+                      : (const void *)gdi_cta_sorted_kernel<BS, 8>;
+}
+
+template <int BS>
+size_t cta_kernel_smem(const GdiDevProblem &P, const GdiDevRun &R)
+{
+    return cta_sorted(P, R) ? cta_sorted_smem(P.max_n, P.max_class, R.max_row, P.W, BS)
+                         : cta_smem(P, R, BS, hist_bins(P));
+}
+
 template <int BS>
 int launch_cta(const GdiDevProblem &P, const GdiDevRun &R, int grid_limit, cudaStream_t st,
                int *grid_used, size_t *smem_used)
 {
-    const int H = hist_bins(P);
-    const size_t smem = cta_smem(P, R, BS, H);
-    cudaError_t e = cudaFuncSetAttribute(gdi_cta_anneal_kernel<BS>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const void *kern = cta_kernel<BS>(P, R);
+    const size_t smem = cta_kernel_smem<BS>(P, R);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return (int)e;
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gdi_cta_anneal_kernel<BS>, BS, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BS, smem);
     if (e != cudaSuccess) return (int)e;
     if (per_sm < 1) return (int)cudaErrorInvalidConfiguration;
     const int items = P.num_instances * P.replicas;
     int grid = sms * per_sm;
     if (grid > items) grid = items;
     if (grid_limit > 0 && grid > grid_limit) grid = grid_limit;
-    gdi_cta_anneal_kernel<BS><<<grid, BS, smem, st>>>(P, R, H);
+    if (cta_sorted(P, R)) {
+        void *args[] = {const_cast<GdiDevProblem *>(&P), const_cast<GdiDevRun *>(&R)};
+        e = cudaLaunchKernel(kern, dim3(grid), dim3(BS), args, smem, st);
+        if (e != cudaSuccess) return (int)e;
+    } else {
+        gdi_cta_anneal_kernel<BS><<<grid, BS, smem, st>>>(P, R, hist_bins(P));
+    }
     if (grid_used) *grid_used = grid;
     if (smem_used) *smem_used = smem;
     return (int)cudaGetLastError();
@@ -488,11 +725,10 @@ int launch_cta(const GdiDevProblem &P, const GdiDevRun &R, int grid_limit, cudaS
 template <int BS>
 int cta_occupancy(const GdiDevProblem &P, const GdiDevRun &R, int *per_sm)
 {
-    const size_t smem = cta_smem(P, R, BS, hist_bins(P));
-    cudaError_t e = cudaFuncSetAttribute(gdi_cta_anneal_kernel<BS>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, gdi_cta_anneal_kernel<BS>, BS, smem);
+    const void *kern = cta_kernel<BS>(P, R);
+    const size_t smem = cta_kernel_smem<BS>(P, R);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, kern, BS, smem);
     return (int)e;
 }
 
@@ -514,7 +750,8 @@ int gdi_cta_smem_bytes(const GdiDevProblem &P, const GdiDevRun &R, int block, si
 {
     const int H = hist_bins(P);
     if (hist) *hist = H;
-    if (bytes) *bytes = cta_smem(P, R, block, H);
+    if (bytes) *bytes = cta_sorted(P, R) ? cta_sorted_smem(P.max_n, P.max_class, R.max_row, P.W, block)
+                                      : cta_smem(P, R, block, H);
     return 0;
 }
 
