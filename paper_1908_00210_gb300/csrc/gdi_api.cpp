@@ -730,19 +730,23 @@ int gdi_anneal(gdi_ctx *c, const gdi_schedule *S, const gdi_run *run)
     if (c->path == GDI_PATH_GRID || (run->flags & GDI_FLAG_RACY)) grid = true;
     else if (run->flags & GDI_FLAG_STANDARD) grid = false;
     else if (c->path == GDI_PATH_AUTO && c->Q == 1 && c->W >= 1 && c->max_degree <= 32767) {
-        // one instance: the cheaper path by a cost model fitted on GB300 (BA and ER graphs of mean
-        // degree 10, 10^3 to 6.4*10^4 vertices, 1 to 608 replicas).  A CTA-resident sweep costs
-        // about 3.5 ns per (vertex + directed edge) per wave of resident blocks; a grid-scale sweep
-        // about 120 us (its per-class grid barriers) + 0.016 ns per (vertex + edge) per group of 8
-        // replicas.  The crossover for 8 replicas is near 3,000 vertices.
+        // one instance: the cheaper path by a cost model fitted on GB300 (BA graphs, m = 5, of
+        // 2*10^3 to 6.4*10^4 vertices; ER graphs of 800 vertices at mean degree 49 and 1.6*10^4 at
+        // 10; 1 to 152 replicas; 100 sweeps).  Per sweep, a CTA-resident block costs about 2 us
+        // per colour class + 1.8 ns (blocks of 128 or 256 threads) or 1.2 ns (512, 1024) per
+        // (vertex + directed edge), per wave of resident blocks; a grid-scale launch costs about
+        // 13 us per colour class (thresholds, sort, chain and barrier) + 0.02 ns per (vertex +
+        // edge), per group of 8 replicas.
         int per_sm = 0;
         if (need > (size_t)max_optin || gdi_cta_blocks_per_sm(P, R, c->block, &per_sm) != 0 || per_sm < 1) {
             grid = true;
         } else {
             const double work = (double)c->N + (double)c->nnz;
+            const double ncls = (double)c->num_classes[0];
             const int64_t slots = (int64_t)sms * per_sm;
-            const double cta_s = (double)((c->R + slots - 1) / slots) * 3.5e-9 * work;
-            const double grid_s = (double)((c->R + 7) / 8) * (120e-6 + 0.016e-9 * work);
+            const double per_work = c->block >= 512 ? 1.2e-9 : 1.8e-9;
+            const double cta_s = (double)((c->R + slots - 1) / slots) * (2e-6 * ncls + per_work * work);
+            const double grid_s = (double)((c->R + 7) / 8) * (13e-6 * ncls + 0.02e-9 * work);
             grid = grid_s < cta_s;
         }
     }

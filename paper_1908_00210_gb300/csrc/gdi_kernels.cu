@@ -453,7 +453,7 @@ __host__ __device__ inline size_t cta_sorted_smem(int32_t max_n, int32_t max_cla
 }
 
 template <int BS, int SL>
-__global__ void __launch_bounds__(BS) gdi_cta_sorted_kernel(GdiDevProblem P, GdiDevRun R)
+__global__ void __launch_bounds__(BS, 1024 / BS) gdi_cta_sorted_kernel(GdiDevProblem P, GdiDevRun R)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem S = {};
@@ -500,6 +500,8 @@ __global__ void __launch_bounds__(BS) gdi_cta_sorted_kernel(GdiDevProblem P, Gdi
         const int32_t *cls = P.class_ptr + P.class_off[q];
         const int32_t ncls = P.class_off[q + 1] - P.class_off[q] - 1;
         int8_t *gsig = R.spins + (int64_t)rep * P.N + base;
+        const int64_t nnz_item = P.row_ptr[base + n] - P.row_ptr[base];
+        const int32_t mean_deg = n > 0 ? (int32_t)min((nnz_item + n - 1) / n, (int64_t)64) : 1;
 
         int32_t g = 0;
         for (int32_t r = threadIdx.x; r < n; r += BS) {
@@ -523,19 +525,52 @@ __global__ void __launch_bounds__(BS) gdi_cta_sorted_kernel(GdiDevProblem P, Gdi
                 const int32_t ns = hi - lo;
                 const int32_t nwin = (ns + W - 1) / W;
                 const int32_t c0 = *S.G;                 // G at class start (the reference c)
-                // thresholds of the class's ranks, one Philox call per aligned quad
-                for (int32_t qd = (lo >> 2) + threadIdx.x; qd <= ((hi - 1) >> 2); qd += BS) {
-                    const uint4 u4 = philox4x32_10(
-                        make_uint4((uint32_t)qd, (uint32_t)sw, (uint32_t)q, (uint32_t)rep), R.key0, R.key1);
+                // lanes per rank for the field sums: a small class of long rows spreads each row
+                // over a team of T lanes (one round of the block); otherwise one thread takes an
+                // aligned quad of ranks with one Philox call
+                int T = 1;
+                while (T < 32 && T < mean_deg && 2 * T * ns <= BS) T <<= 1;
+                if (T == 1) {
+                    for (int32_t qd = (lo >> 2) + threadIdx.x; qd <= ((hi - 1) >> 2); qd += BS) {
+                        const uint4 u4 = philox4x32_10(
+                            make_uint4((uint32_t)qd, (uint32_t)sw, (uint32_t)q, (uint32_t)rep), R.key0, R.key1);
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        const int32_t r = 4 * qd + j;
-                        if (r < lo || r >= hi) continue;
-                        const int sg = S.sig[r];
-                        const int32_t h = local_field(P, base, r, S.sig);
-                        const int32_t es = estar_of(S.row, rlen, R.mode, word_of(u4, j), Tsw);
-                        C.gam[r - lo] = gamma_of(sg, h, es, P.A, P.B);
-                        C.s0[r - lo] = sg < 0 ? 1 : 0;
+                        for (int j = 0; j < 4; ++j) {
+                            const int32_t r = 4 * qd + j;
+                            if (r < lo || r >= hi) continue;
+                            const int sg = S.sig[r];
+                            const int32_t h = local_field(P, base, r, S.sig);
+                            const int32_t es = estar_of(S.row, rlen, R.mode, word_of(u4, j), Tsw);
+                            C.gam[r - lo] = gamma_of(sg, h, es, P.A, P.B);
+                            C.s0[r - lo] = sg < 0 ? 1 : 0;
+                        }
+                    }
+                } else {
+                    // teams are aligned lane groups of one warp; every lane takes part in every
+                    // round's shuffles (the round count is the same for the whole block)
+                    const int sub = threadIdx.x & (T - 1);
+                    for (int32_t k0 = 0; k0 < ns; k0 += BS / T) {
+                        const int32_t i = k0 + (int32_t)threadIdx.x / T;
+                        int32_t h = 0;
+                        if (i < ns) {
+                            const int64_t e0 = P.row_ptr[base + lo + i], e1 = P.row_ptr[base + lo + i + 1];
+                            for (int64_t e = e0 + sub; e < e1; e += T) {
+                                const uint32_t cc = __ldg(P.col + e);
+                                const int32_t sv = S.sig[cc & 0x7FFFFFFFu];
+                                h += (cc >> 31) ? -sv : sv;
+                            }
+                        }
+                        for (int o = T >> 1; o >= 1; o >>= 1) h += __shfl_xor_sync(0xFFFFFFFFu, h, o);
+                        if (i < ns && sub == 0) {
+                            const int32_t r = lo + i;
+                            const uint4 u4 = philox4x32_10(
+                                make_uint4((uint32_t)(r >> 2), (uint32_t)sw, (uint32_t)q, (uint32_t)rep), R.key0,
+                                R.key1);
+                            const int sg = S.sig[r];
+                            const int32_t es = estar_of(S.row, rlen, R.mode, word_of(u4, r & 3), Tsw);
+                            C.gam[i] = gamma_of(sg, h, es, P.A, P.B);
+                            C.s0[i] = sg < 0 ? 1 : 0;
+                        }
                     }
                 }
                 for (int32_t i = threadIdx.x; i < ns / 32 + 2; i += BS) C.fbits[i] = 0;
@@ -669,16 +704,21 @@ int hist_bins(const GdiDevProblem &P)
 }
 
 // the sorted-window kernel serves every window size 1 .. 256 (one instantiation per members per
-// lane) of the running-G method; Algorithm 2 (GDI_DEV_STANDARD) stays on gdi_cta_anneal_kernel
-inline bool cta_sorted(const GdiDevProblem &P, const GdiDevRun &R)
+// lane) of the running-G method when its whole-class buffers fit in a block's shared memory;
+// Algorithm 2 (GDI_DEV_STANDARD), larger windows and larger classes take gdi_cta_anneal_kernel
+inline bool cta_sorted(const GdiDevProblem &P, const GdiDevRun &R, int BS)
 {
-    return P.W >= 1 && P.W <= 256 && !(R.flags & GDI_DEV_STANDARD);
+    if (P.W < 1 || P.W > 256 || (R.flags & GDI_DEV_STANDARD)) return false;
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    return cta_sorted_smem(P.max_n, P.max_class, R.max_row, P.W, BS) <= (size_t)optin;
 }
 
 template <int BS>
 const void *cta_kernel(const GdiDevProblem &P, const GdiDevRun &R)
 {
-    if (!cta_sorted(P, R)) return (const void *)gdi_cta_anneal_kernel<BS>;
+    if (!cta_sorted(P, R, BS)) return (const void *)gdi_cta_anneal_kernel<BS>;
     return P.W <= 32 ? (const void *)gdi_cta_sorted_kernel<BS, 1>
          : P.W <= 64 ? (const void *)gdi_cta_sorted_kernel<BS, 2>
          : P.W <= 128 ? (const void *)gdi_cta_sorted_kernel<BS, 4>
@@ -688,7 +728,7 @@ const void *cta_kernel(const GdiDevProblem &P, const GdiDevRun &R)
 template <int BS>
 size_t cta_kernel_smem(const GdiDevProblem &P, const GdiDevRun &R)
 {
-    return cta_sorted(P, R) ? cta_sorted_smem(P.max_n, P.max_class, R.max_row, P.W, BS)
+    return cta_sorted(P, R, BS) ? cta_sorted_smem(P.max_n, P.max_class, R.max_row, P.W, BS)
                          : cta_smem(P, R, BS, hist_bins(P));
 }
 
@@ -710,7 +750,7 @@ int launch_cta(const GdiDevProblem &P, const GdiDevRun &R, int grid_limit, cudaS
     int grid = sms * per_sm;
     if (grid > items) grid = items;
     if (grid_limit > 0 && grid > grid_limit) grid = grid_limit;
-    if (cta_sorted(P, R)) {
+    if (cta_sorted(P, R, BS)) {
         void *args[] = {const_cast<GdiDevProblem *>(&P), const_cast<GdiDevRun *>(&R)};
         e = cudaLaunchKernel(kern, dim3(grid), dim3(BS), args, smem, st);
         if (e != cudaSuccess) return (int)e;
@@ -750,7 +790,7 @@ int gdi_cta_smem_bytes(const GdiDevProblem &P, const GdiDevRun &R, int block, si
 {
     const int H = hist_bins(P);
     if (hist) *hist = H;
-    if (bytes) *bytes = cta_sorted(P, R) ? cta_sorted_smem(P.max_n, P.max_class, R.max_row, P.W, block)
+    if (bytes) *bytes = cta_sorted(P, R, block) ? cta_sorted_smem(P.max_n, P.max_class, R.max_row, P.W, block)
                                       : cta_smem(P, R, block, H);
     return 0;
 }

@@ -86,11 +86,11 @@ def test_ba1m_all_500_sweeps_every_replica(gdi):
 
 
 def test_torus_all_5000_sweeps_sampled_replicas(gdi):
-    """Torus 100 x 100 (+-1 weights, checkerboard), 64 replicas, W = 1024, 5000 sweeps: replicas
+    """Torus 100 x 100 (+-1 weights, checkerboard), 64 replicas, W = 256, 5000 sweeps: replicas
     0, 21, 42 and 63 replayed by the oracle over the whole schedule."""
     g = torus2d(100, 2002)
-    kw = dict(A=1, B=4, W=1024, t0=12.0, t1=0.2, sweeps=5000, seed=1, color=g.color)
-    ann = gdi.Annealer(g, A=1, B=4, W=1024, replicas=64, color=g.color)
+    kw = dict(A=1, B=4, W=256, t0=12.0, t1=0.2, sweeps=5000, seed=1, color=g.color)
+    ann = gdi.Annealer(g, A=1, B=4, W=256, replicas=64, color=g.color)
     ann.anneal(gdi.Schedule(sweeps=5000, t0=12.0, t1=0.2), 1, flags=gdi.GDI_FLAG_TRACE)
     res, spins, tr = ann.results(), ann.spins(), ann.trace()
     ann.close()
