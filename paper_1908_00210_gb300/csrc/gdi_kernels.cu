@@ -411,8 +411,20 @@ struct SortedCta {
     uint32_t *fbits;    // [max_class / 32 + 2] flips of the fast replay
     uint32_t *fm;       // [max_class / 4 + 2] flips of the exact replay (byte per member)
     int32_t *bins;      // [HA] exact-replay histogram
-    StageMap *maps;     // [warps][2] stage maps (only the narrow flag is used here)
+    StageMap *maps;     // [warps][2] stage maps of the window a warp sorts (classes of many windows)
+    StageMap *wmaps;    // [nwm][2] stage maps of every window (classes of at most nwm windows)
+    int32_t *tin;       // [nwm + 2] entering lattice index of every window; then the walk's
+                        // first failing window and its last lattice index
 };
+
+// windows per class whose stage maps are kept for the walk (more: one warp replays them in order)
+constexpr int CTA_WALK_MAX = 128;
+
+__host__ __device__ inline int cta_walk_windows(int32_t max_class, int W)
+{
+    const int32_t nw = (max_class + W - 1) / W;
+    return nw < CTA_WALK_MAX ? (int)nw : CTA_WALK_MAX;
+}
 
 __host__ __device__ inline size_t align16c(size_t x) { return (x + 15) & ~(size_t)15; }
 
@@ -420,7 +432,7 @@ __host__ __device__ inline size_t align16c(size_t x) { return (x + 15) & ~(size_
 // host's size: the common part (reductions, G, table row, spins, repair flags), then the class
 // buffers.  Every array starts on a 16-byte boundary.
 struct CtaSortedLayout {
-    size_t red64, red32, G, row, sig, flag, gam, rel, s0, narrow, fbits, fm, bins, maps, total;
+    size_t red64, red32, G, row, sig, flag, gam, rel, s0, narrow, fbits, fm, bins, maps, wmaps, tin, total;
 };
 
 __host__ __device__ inline CtaSortedLayout cta_sorted_layout(int32_t max_n, int32_t max_class, int32_t max_row,
@@ -443,6 +455,9 @@ __host__ __device__ inline CtaSortedLayout cta_sorted_layout(int32_t max_n, int3
     L.fm = o; o = align16c(o + 4 * (mc / 4 + 2));
     L.bins = o; o = align16c(o + 4 * (size_t)win::HA);
     L.maps = o; o = align16c(o + sizeof(StageMap) * 2 * (size_t)(BS / 32));
+    const int nwm = cta_walk_windows(max_class, W);
+    L.wmaps = o; o = align16c(o + sizeof(StageMap) * 2 * (size_t)nwm);
+    L.tin = o; o = align16c(o + sizeof(int32_t) * (size_t)(nwm + 2));
     L.total = o;
     return L;
 }
@@ -474,6 +489,8 @@ __global__ void __launch_bounds__(BS, 1024 / BS) gdi_cta_sorted_kernel(GdiDevPro
         C.fm = reinterpret_cast<uint32_t *>(smem_raw + L.fm);
         C.bins = reinterpret_cast<int32_t *>(smem_raw + L.bins);
         C.maps = reinterpret_cast<StageMap *>(smem_raw + L.maps);
+        C.wmaps = reinterpret_cast<StageMap *>(smem_raw + L.wmaps);
+        C.tin = reinterpret_cast<int32_t *>(smem_raw + L.tin);
         // the launch must have given the whole layout (the host sizes it with the same function)
         uint32_t dyn;
         asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
@@ -484,6 +501,7 @@ __global__ void __launch_bounds__(BS, 1024 / BS) gdi_cta_sorted_kernel(GdiDevPro
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int W = P.W;
+    const int nwm = cta_walk_windows(P.max_class, W);
     const int32_t items = P.num_instances * P.replicas;
     __shared__ int32_t next_item;
     while (true) {
@@ -576,18 +594,48 @@ __global__ void __launch_bounds__(BS, 1024 / BS) gdi_cta_sorted_kernel(GdiDevPro
                 for (int32_t i = threadIdx.x; i < ns / 32 + 2; i += BS) C.fbits[i] = 0;
                 for (int32_t i = threadIdx.x; i < ns / 4 + 2; i += BS) C.fm[i] = 0;
                 __syncthreads();
-                // every window sorted by one warp
+                // every window sorted by one warp; a class of 3 to nwm windows keeps every
+                // window's stage maps for the walk below (one or two windows replay in order at
+                // the cost of the walk's extra barrier)
+                const bool walk = nwin >= 3 && nwin <= nwm;
                 for (int32_t kk = warp; kk < nwin; kk += BS / 32) {
                     const int32_t ws = kk * W, wlen = min(W, ns - ws);
-                    window_maps<SL>(C.gam, C.s0, C.rel, ws, wlen, 0, c0, C.maps + 2 * warp);
+                    StageMap *o = walk ? C.wmaps + 2 * kk : C.maps + 2 * warp;
+                    window_maps<SL>(C.gam, C.s0, C.rel, ws, wlen, 0, c0, o);
                     __syncwarp();
-                    if (lane == 0) C.narrow[kk] = (uint8_t)C.maps[2 * warp].narrow;
+                    if (lane == 0) C.narrow[kk] = (uint8_t)o[0].narrow;
                 }
                 __syncthreads();
-                // the windows in rank order, each entered with the G its predecessors left
-                if (warp == 0) {
-                    int32_t x = 0;
-                    for (int32_t kk = 0; kk < nwin; ++kk) {
+                int32_t k_seq = 0;                       // first window the ordered tail replays
+                if (walk) {
+                    // one thread follows x = G - c0 from 0 through the windows' stage maps (lattice
+                    // index t: x = 2 t - NT) up to the first window that leaves the lattice
+                    if (threadIdx.x == 0) {
+                        int t = NT / 2;
+                        int32_t kf = nwin;
+                        for (int32_t kk = 0; kk < nwin; ++kk) {
+                            C.tin[kk] = t;
+                            const int u = stage_apply(C.wmaps[2 * kk + (plus_first ? 1 : 0)],
+                                                      stage_apply(C.wmaps[2 * kk + (plus_first ? 0 : 1)], t));
+                            if (u < 0) { kf = kk; break; }
+                            t = u;
+                        }
+                        C.tin[nwm] = kf;
+                        C.tin[nwm + 1] = t;
+                        if (kf == nwin) *S.G = c0 + 2 * t - NT;
+                    }
+                    __syncthreads();
+                    k_seq = C.tin[nwm];
+                    // the windows before it were entered on the lattice: all replayed at once
+                    for (int32_t kk = warp; kk < k_seq; kk += BS / 32) {
+                        const int32_t ws = kk * W, we = min(ws + W, ns);
+                        replay_window<SL>(C.rel, C.s0, 0, ws, we, 2 * C.tin[kk] - NT, plus_first, C.fbits, W);
+                    }
+                }
+                // the rest in rank order, each entered with the G its predecessors left
+                if (warp == 0 && k_seq < nwin) {
+                    int32_t x = walk ? 2 * C.tin[k_seq] - NT : 0;
+                    for (int32_t kk = k_seq; kk < nwin; ++kk) {
                         const int32_t ws = kk * W, we = min(ws + W, ns);
                         const bool on = C.narrow[kk] ? (x >= -NT && x <= NT - 2) : (x >= -FAST_X && x <= FAST_X);
                         x = on ? replay_window<SL>(C.rel, C.s0, 0, ws, we, x, plus_first, C.fbits, W)

@@ -176,3 +176,23 @@ def test_standard_mode_rejected_on_grid_path(gdi):
     with pytest.raises(gdi.GdiError):
         ann.anneal(gdi.Schedule(sweeps=4), 1, flags=gdi.GDI_FLAG_STANDARD)
     ann.close()
+
+
+@pytest.mark.parametrize("W", [4, 8, 32, 64, 256])
+def test_cta_sorted_walk_and_ordered_tail(gdi, W):
+    """CTA-resident sorted kernel: one-sided starts (all +1, all -1) make G leave the stage maps'
+    lattice in the first sweeps, so the walk stops at a window and the rest of the class replays in
+    rank order; W = 4 gives classes of 200 windows (more than the walk keeps), replayed in order
+    throughout.  Bit-exact to the oracle after every sweep."""
+    g = torus2d(40, 45)
+    init = np.stack([np.ones(g.n), -np.ones(g.n),
+                     np.where(np.arange(g.n) % 3 == 0, -1, 1)]).astype(np.int8)
+    kw = dict(A=1, B=4, W=W, t0=2.0, t1=0.2, sweeps=12, seed=17, color=g.color)
+    ann = gdi.Annealer(g, A=1, B=4, W=W, replicas=3, color=g.color)
+    ann.configure(path=gdi.GDI_PATH_CTA)
+    ann.anneal(gdi.Schedule(sweeps=12, t0=2.0, t1=0.2), 17, init=init, flags=gdi.GDI_FLAG_TRACE)
+    res, spins, tr = ann.results(), ann.spins(), ann.trace()
+    assert ann.last_launch()["path"] == gdi.GDI_PATH_CTA
+    ann.close()
+    ref = oracle.anneal(g, replicas=3, init=init, **kw)
+    assert_parity(res, spins, tr, ref)
