@@ -33,27 +33,41 @@ WORKLOADS = {
     # 500 sweeps, window W = 256: the grid-scale path (every SM on one graph).  Algorithmic bytes
     # of one spin update in the pull form: 4 d (columns) + 4 (row pointer) + d (neighbour spins)
     # + 2 (own spin read and write) = 56 B for d = 10.  traffic: dram__bytes_read.sum +
-    # dram__bytes_write.sum of one 500-sweep launch of the sweep kernel (ncu), or None when the
-    # kernel changed after the counters were taken.
+    # dram__bytes_write.sum of one launch of the sweep kernel (ncu), traffic_l2 its
+    # lts__t_bytes.sum; None when the kernel changed after the counters were taken.
     "ba1m_r8": dict(kind="ba", n=1_000_000, m=5, gseed=4004, A=1, B=4, W=256, replicas=8,
                     sweeps=500, t0=12.0, t1=0.2, seed=1,
-                    roofline=dict(bound="hbm", bytes_per_update=56, traffic=None)),
+                    roofline=dict(bound="hbm", bytes_per_update=56, traffic=53_390_000,
+                                  traffic_l2=61_610_000_000,
+                                  note="the graph stays L2-resident (DRAM traffic: the graph read once); "
+                                       "the kernel is bound by its per-class chain of block waits and "
+                                       "barriers, not by a memory unit")),
     # 2-D torus 100 x 100, +-1 weights, checkerboard colouring, 64 replicas, 5000 sweeps, window
     # W = 256: the CTA-resident path.  26 B per update: 4 x 4 B columns + 4 B row pointer + 4 x 1 B
     # spins + 2 B.
     "torus100_r64": dict(kind="torus", L=100, gseed=2002, A=1, B=4, W=256, replicas=64,
                          sweeps=5000, t0=12.0, t1=0.2, seed=1,
-                         roofline=dict(bound="hbm", bytes_per_update=26, traffic=None)),
+                         roofline=dict(bound="hbm", bytes_per_update=26, traffic=3_000_000,
+                                       traffic_l2=187_180_000,
+                                       note="each replica's graph stays in its SM's L1 (99 % hit rate); "
+                                            "the kernel is issue- and barrier-bound on 64 of 152 SMs")),
     # Erdos-Renyi n = 800, p = 0.06, unit weights, greedy colouring, 1000 sweeps, 1 replica: one
     # block holds the whole instance; latency-bound.  Bytes per update 4 d + 4 + d + 2 at d = 48.7.
     "er800": dict(kind="er", n=800, p=0.06, gseed=1001, A=1, B=4, W=64, replicas=1, sweeps=1000,
-                  t0=12.0, t1=0.2, seed=1, roofline=dict(bound="hbm", bytes_per_update=249.5, traffic=None)),
+                  t0=12.0, t1=0.2, seed=1,
+                  roofline=dict(bound="hbm", bytes_per_update=249.5, traffic=654_850, traffic_l2=11_150_000,
+                                note="one block on one SM: latency-bound (19 colour classes of about "
+                                     "42 vertices per sweep)")),
     # 4,096 Erdos-Renyi instances, n ~ U[800, 3000], mean degree ~ U[3, 48], unit or +-1 weights,
     # one replica each, 2000 sweeps, one persistent launch (CTA-resident, autotuned).  Bytes per
     # update at the batch's mean degree d = 25.5: 4 d + 4 + d + 2 = 134 B.
     "batched4096": dict(kind="batch", count=4096, gseed=3000, n_lo=800, n_hi=3000, A=1, B=4, W=256,
                         replicas=1, sweeps=2000, t0=12.0, t1=0.2, seed=11,
-                        roofline=dict(bound="hbm", bytes_per_update=134, traffic=None)),
+                        roofline=dict(bound="hbm", bytes_per_update=134, traffic=665_799_000_000,
+                                      traffic_l2=1_820_000_000_000,
+                                      note="the 4,096 graphs do not fit in L2: DRAM traffic is about a "
+                                           "third of the algorithmic bytes, at 0.3 of the measured HBM "
+                                           "bandwidth; latency-bound")),
 }
 DEFAULT_WORKLOAD = "ba1m_r8"
 
@@ -288,7 +302,13 @@ def run_ours(args, wl, rank, world, local):
     create_s = time.perf_counter() - t_create
     # CTA-resident workloads: block size and blocks per SM by the library's autotuner (results do
     # not depend on them); the grid-scale workload keeps one 768-thread block per SM
-    tuned = ann.autotune(sch, probe_sweeps=20) if wl["kind"] != "ba" else None
+    if wl["kind"] == "ba":
+        tuned = None
+    elif args.block:
+        ann.configure(block=args.block)
+        tuned = dict(block=args.block, grid=0, ms=None)
+    else:
+        tuned = ann.autotune(sch, probe_sweeps=20)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")
     updates = wl["replicas"] * wl["sweeps"] * g.n
 
@@ -369,9 +389,14 @@ def run_ours(args, wl, rank, world, local):
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": rf.get("traffic"),
                 "algorithmic_bytes_per_update": rf["bytes_per_update"], "kernel_ms_per_launch": kernel_ms,
-                "achieved_note": "algorithmic bytes (pull-form gather of every update) / sweep-kernel time; "
-                                 "the graph stays L2-resident, so DRAM traffic is far below these bytes",
+                "achieved_note": "algorithmic bytes (pull-form gather of every update) / sweep-kernel time",
                 "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
+        if rf.get("traffic_l2"):
+            # lts__t_bytes.sum of one launch (ncu) over the launch's duration
+            roof["traffic_l2"] = rf["traffic_l2"]
+            roof["achieved_l2_gbs"] = rf["traffic_l2"] / (kernel_ms / 1e3) / 1e9
+        if rf.get("note"):
+            roof["note"] = rf["note"]
     else:
         sm_max = float(pk.get("sm_max_mhz", 2070.0))
         peak = dev_props.multi_processor_count * 128 * sm_max * 1e6 / 1e12
@@ -431,6 +456,9 @@ def main():
                     help="profiling only: override the workload's sweep count")
     ap.add_argument("--quick", action="store_true",
                     help="profiling only: skip the CPU baseline and the end-to-end leg")
+    ap.add_argument("--block", type=int, default=0,
+                    help="profiling only: CTA-resident threads per block instead of the autotuner's "
+                         "choice (128/256/512/1024; full occupancy)")
     args = ap.parse_args()
     wl = dict(WORKLOADS[args.workload])
     if args.sweeps > 0:

@@ -95,6 +95,7 @@ struct gdi_ctx {
     DevBuf<int64_t> node_off, row_ptr;
     DevBuf<int32_t> class_off, class_ptr, rank_of;
     DevBuf<uint32_t> col;
+    DevBuf<uint16_t> col16;
     DevBuf<int8_t> spins, init_stage, out_stage;
     DevBuf<uint32_t> tab;
     DevBuf<int32_t> tab_off;
@@ -131,6 +132,7 @@ struct gdi_ctx {
         P.class_ptr = class_ptr.p;
         P.row_ptr = row_ptr.p;
         P.col = col.p;
+        P.col16 = col16.p;
         P.rank_of = rank_of.p;
         P.A = A;
         P.B = B;
@@ -144,7 +146,7 @@ struct gdi_ctx {
     void release()
     {
         node_off.release(); row_ptr.release(); class_off.release(); class_ptr.release();
-        rank_of.release(); col.release(); spins.release(); init_stage.release(); out_stage.release();
+        rank_of.release(); col.release(); col16.release(); spins.release(); init_stage.release(); out_stage.release();
         tab.release(); tab_off.release(); temp.release(); raw_G.release(); final_G.release(); tr_G.release();
         err.release(); raw_cut.release(); final_cut.release(); tr_cut.release(); tr_digest.release();
         g_packed.release(); g_rflags.release(); g_tables.release(); g_gin.release(); g_Gcls.release();
@@ -513,6 +515,13 @@ int gdi_create(gdi_ctx **out, const gdi_graph *g, const gdi_model *m)
     GDI_UP(c->node_off, inst);
     GDI_UP(c->row_ptr, rp);
     GDI_UP(c->col, cr);
+    if (H.max_n <= 32767) {
+        // 16-bit columns for the CTA-resident kernels' neighbour sums (half the CSR bytes)
+        std::vector<uint16_t> c16(cr.size());
+        for (size_t e = 0; e < cr.size(); ++e)
+            c16[e] = (uint16_t)((cr[e] & 0x7FFFu) | ((cr[e] >> 31) << 15));
+        GDI_UP(c->col16, c16);
+    }
     GDI_UP(c->class_off, class_off);
     GDI_UP(c->class_ptr, class_ptr);
     GDI_UP(c->rank_of, rank_of);

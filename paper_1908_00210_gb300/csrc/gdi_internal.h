@@ -18,6 +18,8 @@ struct GdiDevProblem {
     const int32_t *class_ptr;        // per instance: C_q + 1 class boundaries in local ranks
     const int64_t *row_ptr;          // [N+1] rank-space CSR offsets
     const uint32_t *col;             // [nnz] local neighbour rank | (weight < 0) << 31
+    const uint16_t *col16;           // [nnz] the same in 16 bits (rank | (weight < 0) << 15) when
+                                     // every instance has at most 32,767 vertices, else null
     const int32_t *rank_of;          // [N] original vertex -> global rank
     int32_t A, B, W;
     int32_t max_n;                   // largest instance
@@ -31,7 +33,7 @@ struct GdiGridScratch {
     uint8_t *packed;                 // [N] spins of one replica group: bit r set = replica r is -1
     int16_t *tables;                 // [P][8][TW] composed window tables of every block (W > 256);
                                      // for W <= 256 the same bytes hold the sorted path's exact-G
-                                     // words, table-ready flags and [P][8][64] byte tables
+                                     // words and [P][8][64] byte block and run tables
     int32_t *gin;                    // [P][8] exact G entering every block's windows
     int32_t *Gcls;                   // [8] G at class start / after the class
     unsigned int *bar;               // [4] grid barrier: 64-bit arrival count, gate, unused

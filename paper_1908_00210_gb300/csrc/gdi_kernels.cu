@@ -62,6 +62,20 @@ __device__ __forceinline__ int32_t local_field(const GdiDevProblem &P, int64_t b
     return h;
 }
 
+// the same sum over the 16-bit column copy (instances of at most 32,767 vertices)
+__device__ __forceinline__ int32_t local_field16(const GdiDevProblem &P, int64_t base, int32_t r,
+                                                 const int8_t *sig)
+{
+    const int64_t e0 = P.row_ptr[base + r], e1 = P.row_ptr[base + r + 1];
+    int32_t h = 0;
+    for (int64_t e = e0; e < e1; ++e) {
+        const uint32_t c = __ldg(P.col16 + e);
+        const int32_t s = sig[c & 0x7FFFu];
+        h += (c >> 15) ? -s : s;
+    }
+    return h;
+}
+
 // count of members of group grp with d >= x (exact d), block-wide
 template <int BS>
 __device__ int32_t count_ge(const Smem &S, int32_t Wn, int grp, int32_t Gc, int64_t x)
@@ -557,7 +571,7 @@ __global__ void __launch_bounds__(BS, 1024 / BS) gdi_cta_sorted_kernel(GdiDevPro
                             const int32_t r = 4 * qd + j;
                             if (r < lo || r >= hi) continue;
                             const int sg = S.sig[r];
-                            const int32_t h = local_field(P, base, r, S.sig);
+                            const int32_t h = P.col16 ? local_field16(P, base, r, S.sig) : local_field(P, base, r, S.sig);
                             const int32_t es = estar_of(S.row, rlen, R.mode, word_of(u4, j), Tsw);
                             C.gam[r - lo] = gamma_of(sg, h, es, P.A, P.B);
                             C.s0[r - lo] = sg < 0 ? 1 : 0;
@@ -572,10 +586,18 @@ __global__ void __launch_bounds__(BS, 1024 / BS) gdi_cta_sorted_kernel(GdiDevPro
                         int32_t h = 0;
                         if (i < ns) {
                             const int64_t e0 = P.row_ptr[base + lo + i], e1 = P.row_ptr[base + lo + i + 1];
-                            for (int64_t e = e0 + sub; e < e1; e += T) {
-                                const uint32_t cc = __ldg(P.col + e);
-                                const int32_t sv = S.sig[cc & 0x7FFFFFFFu];
-                                h += (cc >> 31) ? -sv : sv;
+                            if (P.col16) {
+                                for (int64_t e = e0 + sub; e < e1; e += T) {
+                                    const uint32_t cc = __ldg(P.col16 + e);
+                                    const int32_t sv = S.sig[cc & 0x7FFFu];
+                                    h += (cc >> 15) ? -sv : sv;
+                                }
+                            } else {
+                                for (int64_t e = e0 + sub; e < e1; e += T) {
+                                    const uint32_t cc = __ldg(P.col + e);
+                                    const int32_t sv = S.sig[cc & 0x7FFFFFFFu];
+                                    h += (cc >> 31) ? -sv : sv;
+                                }
                             }
                         }
                         for (int o = T >> 1; o >= 1; o >>= 1) h += __shfl_xor_sync(0xFFFFFFFFu, h, o);

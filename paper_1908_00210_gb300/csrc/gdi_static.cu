@@ -177,6 +177,7 @@ extern "C" int gdi_anneal_static(int32_t n, const int64_t *row_ptr, const uint32
     P.class_ptr = class_ptr;
     P.row_ptr = row_ptr;
     P.col = col;
+    P.col16 = nullptr;
     P.rank_of = nullptr;
     P.A = A;
     P.B = B;

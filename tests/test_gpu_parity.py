@@ -196,3 +196,18 @@ def test_cta_sorted_walk_and_ordered_tail(gdi, W):
     ann.close()
     ref = oracle.anneal(g, replicas=3, init=init, **kw)
     assert_parity(res, spins, tr, ref)
+
+
+def test_cta_sorted_32bit_columns(gdi):
+    """An instance above 32,767 vertices on the CTA-resident sorted kernel: the neighbour sums read
+    the 32-bit columns (smaller instances read the 16-bit copy)."""
+    g = barabasi_albert(40000, 5, 47)
+    kw = dict(A=1, B=4, W=64, t0=12.0, t1=0.2, sweeps=6, seed=23)
+    ann = gdi.Annealer(g, A=1, B=4, W=64, replicas=2)
+    ann.configure(path=gdi.GDI_PATH_CTA)
+    ann.anneal(gdi.Schedule(sweeps=6, t0=12.0, t1=0.2), 23, flags=gdi.GDI_FLAG_TRACE)
+    res, spins, tr = ann.results(), ann.spins(), ann.trace()
+    assert ann.last_launch()["path"] == gdi.GDI_PATH_CTA
+    ann.close()
+    ref = oracle.anneal(g, replicas=2, **kw)
+    assert_parity(res, spins, tr, ref)
