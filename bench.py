@@ -165,8 +165,10 @@ class ClockSampler:
 def oracle_throughput(g, wl, seconds: float = 12.0, processes: int | None = None):
     """The oracle as it stands, timed on the host cores on a bounded sample of the workload: each
     worker process anneals up to 4 replicas of the graph (for a batch: 4 of its instances, a
-    different set per process) for as many sweeps of the same schedule as fit the time budget
-    (decided from a one-sweep probe).  Returns (updates/s, cores, sample text)."""
+    different set per process) for as many sweeps of the same schedule as fit the time budget, and
+    repeats the whole anneal with other seeds while the budget lasts when the schedule is shorter
+    than it.  The cost of a sweep and of a call's setup come from two probes (1 and 3 sweeps).
+    Returns (updates/s, cores, sample text)."""
     import multiprocessing as mp
     import oracle
     oracle.build()
@@ -174,25 +176,31 @@ def oracle_throughput(g, wl, seconds: float = 12.0, processes: int | None = None
     R = min(4, wl["replicas"])
     parts = getattr(g, "parts", None)
     sets = [_inst_set(parts, k) for k in range(cores)] if parts else [None] * cores
-    t = time.perf_counter()
-    _oracle_worker((g if parts is None else sets[0], wl, R, 1, 0))
-    per_sweep = max(time.perf_counter() - t, 1e-4)
-    sweeps = int(max(1, min(wl["sweeps"], seconds / per_sweep)))
+    probe = []
+    for sw in (1, 3):
+        t = time.perf_counter()
+        _oracle_worker((g if parts is None else sets[0], wl, R, sw, 0, 0.0))
+        probe.append(time.perf_counter() - t)
+    per_sweep = max((probe[1] - probe[0]) / 2, 1e-5)
+    setup = max(probe[0] - per_sweep, 0.0)
+    sweeps = int(max(1, min(wl["sweeps"], (seconds - setup) / per_sweep)))
+    # a schedule shorter than the budget is annealed again (other seeds) until the budget is spent
+    budget = 0.0 if sweeps < wl["sweeps"] else seconds
     ctx = mp.get_context("spawn")
-    args = [(g if parts is None else sets[k], wl, R, sweeps, k) for k in range(cores)]
+    args = [(g if parts is None else sets[k], wl, R, sweeps, k, budget) for k in range(cores)]
     t0 = time.perf_counter()
     with ctx.Pool(cores) as pool:
-        pool.map(_oracle_worker, args)
+        done = pool.map(_oracle_worker, args)
     dt = time.perf_counter() - t0
+    reps = sum(done) / len(done)
     if parts is None:
-        updates = cores * R * sweeps * g.n
-        sample = (f"{cores} processes x {R} replicas x first {sweeps} of {wl['sweeps']} sweeps "
-                  f"x {g.n} spins = {updates:.3e} updates in {dt:.1f} s")
+        updates = sum(done) * R * sweeps * g.n
+        sample = (f"{cores} processes x {reps:.1f} anneals x {R} replicas x first {sweeps} of {wl['sweeps']} "
+                  f"sweeps x {g.n} spins = {updates:.3e} updates in {dt:.1f} s")
     else:
-        spins = sum(sum(x.n for x in st) for st in sets)
-        updates = R * sweeps * spins
-        sample = (f"{cores} processes x 4 instances of the batch x {R} replica x first {sweeps} of "
-                  f"{wl['sweeps']} sweeps ({spins} spins) = {updates:.3e} updates in {dt:.1f} s")
+        updates = sum(d * R * sweeps * sum(x.n for x in st) for d, st in zip(done, sets))
+        sample = (f"{cores} processes x {reps:.1f} anneals x 4 instances of the batch x {R} replica x first "
+                  f"{sweeps} of {wl['sweeps']} sweeps = {updates:.3e} updates in {dt:.1f} s")
     return updates / dt, cores, sample
 
 
@@ -202,13 +210,19 @@ def _inst_set(parts, k):
 
 
 def _oracle_worker(a):
-    g, wl, R, sweeps, k = a
+    """Anneal the sample once, then again with other seeds while the time budget lasts; returns
+    the number of anneals."""
+    g, wl, R, sweeps, k, budget = a
     import oracle
-    for x in (g if isinstance(g, list) else [g]):
-        oracle.anneal(x, A=wl["A"], B=wl["B"], W=wl["W"], t0=wl["t0"], t1=wl["t1"], sweeps=wl["sweeps"],
-                      seed=wl["seed"] + 1000 * k, replicas=R, color=x.color, last_sweep=sweeps,
-                      trace=False, repair=False)
-    return 0
+    t_end = time.perf_counter() + budget
+    rep = 0
+    while rep == 0 or time.perf_counter() < t_end:
+        for x in (g if isinstance(g, list) else [g]):
+            oracle.anneal(x, A=wl["A"], B=wl["B"], W=wl["W"], t0=wl["t0"], t1=wl["t1"], sweeps=wl["sweeps"],
+                          seed=wl["seed"] + 1000 * k + 100_000 * rep, replicas=R, color=x.color,
+                          last_sweep=sweeps, trace=False, repair=False)
+        rep += 1
+    return rep
 
 
 # ---------------------------------------------------------------------------------------------
