@@ -23,6 +23,7 @@
 //      sums; ties at d* are resolved by rank with a block prefix count.
 //   3. G changes by -2K (+1 group) or +2K (-1 group): one shared-memory update per group, the
 //      block-level analogue of the paper's atomicAdd on G.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -422,8 +423,8 @@ struct SortedCta {
     int16_t *rel;       // [max_class] comparison values
     uint8_t *s0;        // [max_class] 1 = the member was -1 at window start
     uint8_t *narrow;    // [windows of the largest class] window sorted with 16-bit keys
-    uint32_t *fbits;    // [max_class / 32 + 2] flips of the fast replay
-    uint32_t *fm;       // [max_class / 4 + 2] flips of the exact replay (byte per member)
+    uint32_t *fbits;    // [2][max_class / 32 + 2] flips of the fast replay (two class buffers)
+    uint32_t *fm;       // [2][max_class / 4 + 2] flips of the exact replay (byte per member)
     int32_t *bins;      // [HA] exact-replay histogram
     StageMap *maps;     // [warps][2] stage maps of the window a warp sorts (classes of many windows)
     StageMap *wmaps;    // [nwm][2] stage maps of every window (classes of at most nwm windows)
@@ -465,8 +466,8 @@ __host__ __device__ inline CtaSortedLayout cta_sorted_layout(int32_t max_n, int3
     L.rel = o; o = align16c(o + 2 * mc);
     L.s0 = o; o = align16c(o + mc);
     L.narrow = o; o = align16c(o + (size_t)((max_class + W - 1) / W) + 4);
-    L.fbits = o; o = align16c(o + 4 * (mc / 32 + 2));
-    L.fm = o; o = align16c(o + 4 * (mc / 4 + 2));
+    L.fbits = o; o = align16c(o + 2 * 4 * (mc / 32 + 2));
+    L.fm = o; o = align16c(o + 2 * 4 * (mc / 4 + 2));
     L.bins = o; o = align16c(o + 4 * (size_t)win::HA);
     L.maps = o; o = align16c(o + sizeof(StageMap) * 2 * (size_t)(BS / 32));
     const int nwm = cta_walk_windows(max_class, W);
@@ -481,7 +482,13 @@ __host__ __device__ inline size_t cta_sorted_smem(int32_t max_n, int32_t max_cla
     return cta_sorted_layout(max_n, max_class, max_row, W, BS).total;
 }
 
-template <int BS, int SL>
+// PAIR: a cluster of two blocks anneals each item.  Both keep all spins and G; a class of 3 to
+// nwm windows is split in two halves of windows (thresholds, sorts and replays each block's own),
+// the walk reads the other block's stage maps through distributed shared memory, and each block
+// applies the whole class's flips from both blocks' bitmaps.  Other classes are done by block 0
+// alone.  Flip bitmaps alternate between two buffers from class to class, so a block may clear
+// the next class's buffer while its partner still reads the current one.
+template <int BS, int SL, bool PAIR>
 __global__ void __launch_bounds__(BS, 1024 / BS) gdi_cta_sorted_kernel(GdiDevProblem P, GdiDevRun R)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -517,11 +524,24 @@ __global__ void __launch_bounds__(BS, 1024 / BS) gdi_cta_sorted_kernel(GdiDevPro
     const int W = P.W;
     const int nwm = cta_walk_windows(P.max_class, W);
     const int32_t items = P.num_instances * P.replicas;
+    const size_t fbw = ((size_t)P.max_class + 8) / 32 + 2, fmw = ((size_t)P.max_class + 8) / 4 + 2;
     __shared__ int32_t next_item;
+    unsigned crank = 0;                                  // block rank in the cluster
+    if constexpr (PAIR) crank = cooperative_groups::this_cluster().block_rank();
+    // the partner block's copy of a shared-memory object (same layout in both blocks)
+    auto peer = [&](auto *ptr) { return cooperative_groups::this_cluster().map_shared_rank(ptr, crank ^ 1u); };
+    auto pair_sync = [&]() {
+        if constexpr (PAIR) cooperative_groups::this_cluster().sync();
+        else __syncthreads();
+    };
     while (true) {
-        __syncthreads();
-        if (threadIdx.x == 0) next_item = atomicAdd(R.item_counter, 1);
-        __syncthreads();
+        pair_sync();
+        if (crank == 0 && threadIdx.x == 0) {
+            const int32_t t = atomicAdd(R.item_counter, 1);
+            next_item = t;
+            if constexpr (PAIR) *peer(&next_item) = t;
+        }
+        pair_sync();
         const int32_t slot = next_item;
         if (slot >= items) break;
         const int32_t item = R.item_order[slot];
@@ -544,6 +564,7 @@ __global__ void __launch_bounds__(BS, 1024 / BS) gdi_cta_sorted_kernel(GdiDevPro
         g = block_sum<BS, int32_t>(g, S.red32);
         if (threadIdx.x == 0) *S.G = g;
         __syncthreads();
+        uint32_t cc = 0;                                 // classes annealed so far (buffer parity)
 
         for (int32_t sw = R.s_begin; sw < R.s_end; ++sw) {
             const int32_t roff = R.tab_off[sw];
@@ -557,19 +578,31 @@ __global__ void __launch_bounds__(BS, 1024 / BS) gdi_cta_sorted_kernel(GdiDevPro
                 const int32_t ns = hi - lo;
                 const int32_t nwin = (ns + W - 1) / W;
                 const int32_t c0 = *S.G;                 // G at class start (the reference c)
+                uint32_t *fb = C.fbits + (PAIR ? (cc & 1u) * fbw : 0);
+                uint32_t *fmm = C.fm + (PAIR ? (cc & 1u) * fmw : 0);
+                ++cc;
+                // a class of 3 to nwm windows keeps every window's stage maps for the walk below
+                // (one or two windows replay in order at the cost of the walk's extra barrier);
+                // a pair splits such a class: windows [0, kmid) are block 0's, the rest block 1's
+                const bool walk = nwin >= 3 && nwin <= nwm;
+                const bool split = PAIR && walk;
+                const int32_t kmid = split ? (nwin + 1) / 2 : nwin;
+                const int32_t kb = crank ? kmid : 0, ke = crank ? nwin : kmid;
+                const int32_t rb = min(kb * W, ns), re = min(ke * W, ns);     // my ranks in the class
+                const int32_t nown = re - rb;
                 // lanes per rank for the field sums: a small class of long rows spreads each row
                 // over a team of T lanes (one round of the block); otherwise one thread takes an
                 // aligned quad of ranks with one Philox call
                 int T = 1;
-                while (T < 32 && T < mean_deg && 2 * T * ns <= BS) T <<= 1;
+                while (T < 32 && T < mean_deg && 2 * T * nown <= BS) T <<= 1;
                 if (T == 1) {
-                    for (int32_t qd = (lo >> 2) + threadIdx.x; qd <= ((hi - 1) >> 2); qd += BS) {
+                    for (int32_t qd = ((lo + rb) >> 2) + threadIdx.x; nown > 0 && qd <= ((lo + re - 1) >> 2); qd += BS) {
                         const uint4 u4 = philox4x32_10(
                             make_uint4((uint32_t)qd, (uint32_t)sw, (uint32_t)q, (uint32_t)rep), R.key0, R.key1);
 #pragma unroll
                         for (int j = 0; j < 4; ++j) {
                             const int32_t r = 4 * qd + j;
-                            if (r < lo || r >= hi) continue;
+                            if (r < lo + rb || r >= lo + re) continue;
                             const int sg = S.sig[r];
                             const int32_t h = P.col16 ? local_field16(P, base, r, S.sig) : local_field(P, base, r, S.sig);
                             const int32_t es = estar_of(S.row, rlen, R.mode, word_of(u4, j), Tsw);
@@ -581,10 +614,10 @@ __global__ void __launch_bounds__(BS, 1024 / BS) gdi_cta_sorted_kernel(GdiDevPro
                     // teams are aligned lane groups of one warp; every lane takes part in every
                     // round's shuffles (the round count is the same for the whole block)
                     const int sub = threadIdx.x & (T - 1);
-                    for (int32_t k0 = 0; k0 < ns; k0 += BS / T) {
+                    for (int32_t k0 = rb; k0 < re; k0 += BS / T) {
                         const int32_t i = k0 + (int32_t)threadIdx.x / T;
                         int32_t h = 0;
-                        if (i < ns) {
+                        if (i < re) {
                             const int64_t e0 = P.row_ptr[base + lo + i], e1 = P.row_ptr[base + lo + i + 1];
                             if (P.col16) {
                                 for (int64_t e = e0 + sub; e < e1; e += T) {
@@ -601,7 +634,7 @@ __global__ void __launch_bounds__(BS, 1024 / BS) gdi_cta_sorted_kernel(GdiDevPro
                             }
                         }
                         for (int o = T >> 1; o >= 1; o >>= 1) h += __shfl_xor_sync(0xFFFFFFFFu, h, o);
-                        if (i < ns && sub == 0) {
+                        if (i < re && sub == 0) {
                             const int32_t r = lo + i;
                             const uint4 u4 = philox4x32_10(
                                 make_uint4((uint32_t)(r >> 2), (uint32_t)sw, (uint32_t)q, (uint32_t)rep), R.key0,
@@ -613,32 +646,34 @@ __global__ void __launch_bounds__(BS, 1024 / BS) gdi_cta_sorted_kernel(GdiDevPro
                         }
                     }
                 }
-                for (int32_t i = threadIdx.x; i < ns / 32 + 2; i += BS) C.fbits[i] = 0;
-                for (int32_t i = threadIdx.x; i < ns / 4 + 2; i += BS) C.fm[i] = 0;
+                for (int32_t i = threadIdx.x; i < ns / 32 + 2; i += BS) fb[i] = 0;
+                for (int32_t i = threadIdx.x; i < ns / 4 + 2; i += BS) fmm[i] = 0;
                 __syncthreads();
-                // every window sorted by one warp; a class of 3 to nwm windows keeps every
-                // window's stage maps for the walk below (one or two windows replay in order at
-                // the cost of the walk's extra barrier)
-                const bool walk = nwin >= 3 && nwin <= nwm;
-                for (int32_t kk = warp; kk < nwin; kk += BS / 32) {
+                // every window of mine sorted by one warp
+                for (int32_t kk = kb + warp; kk < ke; kk += BS / 32) {
                     const int32_t ws = kk * W, wlen = min(W, ns - ws);
                     StageMap *o = walk ? C.wmaps + 2 * kk : C.maps + 2 * warp;
                     window_maps<SL>(C.gam, C.s0, C.rel, ws, wlen, 0, c0, o);
                     __syncwarp();
                     if (lane == 0) C.narrow[kk] = (uint8_t)o[0].narrow;
                 }
-                __syncthreads();
+                // (a pair meets here for every class: the tail below may write the partner's G,
+                // which the partner must have read as this class's c0 first)
+                pair_sync();
                 int32_t k_seq = 0;                       // first window the ordered tail replays
                 if (walk) {
                     // one thread follows x = G - c0 from 0 through the windows' stage maps (lattice
-                    // index t: x = 2 t - NT) up to the first window that leaves the lattice
+                    // index t: x = 2 t - NT) up to the first window that leaves the lattice; in a
+                    // pair both blocks walk (the same result), the partner's maps read remotely
                     if (threadIdx.x == 0) {
+                        const StageMap *own = C.wmaps, *other = PAIR ? peer(C.wmaps) : C.wmaps;
                         int t = NT / 2;
                         int32_t kf = nwin;
                         for (int32_t kk = 0; kk < nwin; ++kk) {
                             C.tin[kk] = t;
-                            const int u = stage_apply(C.wmaps[2 * kk + (plus_first ? 1 : 0)],
-                                                      stage_apply(C.wmaps[2 * kk + (plus_first ? 0 : 1)], t));
+                            const StageMap *wm = ((kk >= kmid) == (crank != 0)) ? own : other;
+                            const int u = stage_apply(wm[2 * kk + (plus_first ? 1 : 0)],
+                                                      stage_apply(wm[2 * kk + (plus_first ? 0 : 1)], t));
                             if (u < 0) { kf = kk; break; }
                             t = u;
                         }
@@ -648,27 +683,50 @@ __global__ void __launch_bounds__(BS, 1024 / BS) gdi_cta_sorted_kernel(GdiDevPro
                     }
                     __syncthreads();
                     k_seq = C.tin[nwm];
-                    // the windows before it were entered on the lattice: all replayed at once
-                    for (int32_t kk = warp; kk < k_seq; kk += BS / 32) {
+                    // my windows before it were entered on the lattice: all replayed at once
+                    for (int32_t kk = kb + warp; kk < min(ke, k_seq); kk += BS / 32) {
                         const int32_t ws = kk * W, we = min(ws + W, ns);
-                        replay_window<SL>(C.rel, C.s0, 0, ws, we, 2 * C.tin[kk] - NT, plus_first, C.fbits, W);
+                        replay_window<SL>(C.rel, C.s0, 0, ws, we, 2 * C.tin[kk] - NT, plus_first, fb, W);
                     }
                 }
-                // the rest in rank order, each entered with the G its predecessors left
-                if (warp == 0 && k_seq < nwin) {
+                // the rest in rank order by one warp of block 0, each window entered with the G its
+                // predecessors left; a window of block 1 is read, and its flips written, remotely
+                if (crank == 0 && warp == 0 && k_seq < nwin) {
                     int32_t x = walk ? 2 * C.tin[k_seq] - NT : 0;
                     for (int32_t kk = k_seq; kk < nwin; ++kk) {
+                        const bool mine = kk < kmid;
+                        const int16_t *rel = C.rel;
+                        const uint8_t *s0 = C.s0, *nar = C.narrow;
+                        const int32_t *gam = C.gam;
+                        uint32_t *fbo = fb, *fmo = fmm;
+                        if constexpr (PAIR) {
+                            if (!mine) {
+                                rel = peer(C.rel); s0 = peer(C.s0); nar = peer(C.narrow);
+                                gam = peer(C.gam); fbo = peer(fb); fmo = peer(fmm);
+                            }
+                        }
                         const int32_t ws = kk * W, we = min(ws + W, ns);
-                        const bool on = C.narrow[kk] ? (x >= -NT && x <= NT - 2) : (x >= -FAST_X && x <= FAST_X);
-                        x = on ? replay_window<SL>(C.rel, C.s0, 0, ws, we, x, plus_first, C.fbits, W)
-                               : window_replay_exact(C.gam, C.s0, 0, ws, we, c0 + x, plus_first, C.bins, C.fm) - c0;
+                        const bool on = nar[kk] ? (x >= -NT && x <= NT - 2) : (x >= -FAST_X && x <= FAST_X);
+                        x = on ? replay_window<SL>(rel, s0, 0, ws, we, x, plus_first, fbo, W)
+                               : window_replay_exact(gam, s0, 0, ws, we, c0 + x, plus_first, C.bins, fmo) - c0;
                     }
-                    if (lane == 0) *S.G = c0 + x;
+                    if (lane == 0) {
+                        *S.G = c0 + x;
+                        if constexpr (PAIR) *peer(S.G) = c0 + x;
+                    }
                 }
-                __syncthreads();
-                for (int32_t i = threadIdx.x; i < ns; i += BS) {
-                    const uint32_t f = ((C.fbits[i >> 5] >> (i & 31)) | (C.fm[i >> 2] >> (8 * (i & 3)))) & 1u;
-                    if (f) S.sig[lo + i] = (int8_t)-S.sig[lo + i];
+                if constexpr (PAIR) pair_sync(); else __syncthreads();
+                // every block applies the whole class's flips to its copy of the spins
+                for (int part = 0; part < (PAIR ? 2 : 1); ++part) {
+                    const int32_t i0 = part == 0 ? 0 : min(kmid * W, ns), i1 = part == 0 ? min(kmid * W, ns) : ns;
+                    const uint32_t *fbr = fb, *fmr = fmm;
+                    if constexpr (PAIR) {
+                        if ((unsigned)part != crank) { fbr = peer(fb); fmr = peer(fmm); }
+                    }
+                    for (int32_t i = i0 + threadIdx.x; i < i1; i += BS) {
+                        const uint32_t f = ((fbr[i >> 5] >> (i & 31)) | (fmr[i >> 2] >> (8 * (i & 3)))) & 1u;
+                        if (f) S.sig[lo + i] = (int8_t)-S.sig[lo + i];
+                    }
                 }
                 __syncthreads();
             }
@@ -680,7 +738,7 @@ __global__ void __launch_bounds__(BS, 1024 / BS) gdi_cta_sorted_kernel(GdiDevPro
                                              ((uint64_t)(rep & 0xFFFF) << 48));
                 dg = block_sum<BS, uint64_t>(dg, reinterpret_cast<uint64_t *>(S.red64));
                 const int64_t ct = item_cut<BS>(P, base, n, S);
-                if (threadIdx.x == 0) {
+                if (threadIdx.x == 0 && crank == 0) {
                     const int64_t o = (int64_t)item * R.sweeps + sw;
                     R.tr_digest[o] = dg;
                     R.tr_G[o] = *S.G;
@@ -695,13 +753,15 @@ __global__ void __launch_bounds__(BS, 1024 / BS) gdi_cta_sorted_kernel(GdiDevPro
         if (!(R.flags & GDI_DEV_NO_REPAIR)) repair<BS>(P, base, n, S);
         const int64_t fin_cut = item_cut<BS>(P, base, n, S);
         __syncthreads();
-        if (threadIdx.x == 0) {
-            R.raw_G[item] = raw_G;
-            R.raw_cut[item] = raw_cut;
-            R.final_G[item] = *S.G;
-            R.final_cut[item] = fin_cut;
+        if (crank == 0) {
+            if (threadIdx.x == 0) {
+                R.raw_G[item] = raw_G;
+                R.raw_cut[item] = raw_cut;
+                R.final_G[item] = *S.G;
+                R.final_cut[item] = fin_cut;
+            }
+            for (int32_t r = threadIdx.x; r < n; r += BS) gsig[r] = S.sig[r];
         }
-        for (int32_t r = threadIdx.x; r < n; r += BS) gsig[r] = S.sig[r];
         __syncthreads();
     }
 }
@@ -785,14 +845,33 @@ inline bool cta_sorted(const GdiDevProblem &P, const GdiDevRun &R, int BS)
     return cta_sorted_smem(P.max_n, P.max_class, R.max_row, P.W, BS) <= (size_t)optin;
 }
 
+// a pair of blocks per item when the items fill at most half of the SMs and the largest class
+// has enough windows (8 to the walk's limit) for two halves
+inline bool cta_pair(const GdiDevProblem &P, const GdiDevRun &R, int BS)
+{
+    if (!cta_sorted(P, R, BS)) return false;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t items = (int64_t)P.num_instances * P.replicas;
+    const int32_t nw = (P.max_class + P.W - 1) / P.W;
+    return 2 * items <= sms && nw >= 8 && nw <= CTA_WALK_MAX;
+}
+
+template <int BS, bool PAIR>
+const void *cta_sorted_kernel_for(int W)
+{
+    return W <= 32 ? (const void *)gdi_cta_sorted_kernel<BS, 1, PAIR>
+         : W <= 64 ? (const void *)gdi_cta_sorted_kernel<BS, 2, PAIR>
+         : W <= 128 ? (const void *)gdi_cta_sorted_kernel<BS, 4, PAIR>
+                    : (const void *)gdi_cta_sorted_kernel<BS, 8, PAIR>;
+}
+
 template <int BS>
 const void *cta_kernel(const GdiDevProblem &P, const GdiDevRun &R)
 {
     if (!cta_sorted(P, R, BS)) return (const void *)gdi_cta_anneal_kernel<BS>;
-    return P.W <= 32 ? (const void *)gdi_cta_sorted_kernel<BS, 1>
-         : P.W <= 64 ? (const void *)gdi_cta_sorted_kernel<BS, 2>
-         : P.W <= 128 ? (const void *)gdi_cta_sorted_kernel<BS, 4>
-                      : (const void *)gdi_cta_sorted_kernel<BS, 8>;
+    return cta_pair(P, R, BS) ? cta_sorted_kernel_for<BS, true>(P.W) : cta_sorted_kernel_for<BS, false>(P.W);
 }
 
 template <int BS>
@@ -820,7 +899,31 @@ int launch_cta(const GdiDevProblem &P, const GdiDevRun &R, int grid_limit, cudaS
     int grid = sms * per_sm;
     if (grid > items) grid = items;
     if (grid_limit > 0 && grid > grid_limit) grid = grid_limit;
-    if (cta_sorted(P, R, BS)) {
+    if (cta_pair(P, R, BS)) {
+        // clusters of two blocks, one item per cluster
+        void *args[] = {const_cast<GdiDevProblem *>(&P), const_cast<GdiDevRun *>(&R)};
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = 2;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(2 * items);
+        cfg.blockDim = dim3(BS);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = st;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int ncl = 0;
+        e = cudaOccupancyMaxActiveClusters(&ncl, kern, &cfg);
+        if (e != cudaSuccess) return (int)e;
+        if (ncl < 1) return (int)cudaErrorInvalidConfiguration;
+        grid = 2 * (items < ncl ? items : ncl);
+        if (grid_limit > 0 && grid > grid_limit) grid = grid_limit >= 2 ? (grid_limit & ~1) : 2;
+        cfg.gridDim = dim3(grid);
+        e = cudaLaunchKernelExC(&cfg, kern, args);
+        if (e != cudaSuccess) return (int)e;
+    } else if (cta_sorted(P, R, BS)) {
         void *args[] = {const_cast<GdiDevProblem *>(&P), const_cast<GdiDevRun *>(&R)};
         e = cudaLaunchKernel(kern, dim3(grid), dim3(BS), args, smem, st);
         if (e != cudaSuccess) return (int)e;
