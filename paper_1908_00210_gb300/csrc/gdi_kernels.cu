@@ -434,6 +434,7 @@ struct SortedCta {
 
 // windows per class whose stage maps are kept for the walk (more: one warp replays them in order)
 constexpr int CTA_WALK_MAX = 128;
+static_assert(sizeof(StageMap) == 16, "a pair copies stage maps as 16-byte words");
 
 __host__ __device__ inline int cta_walk_windows(int32_t max_class, int W)
 {
@@ -661,17 +662,25 @@ __global__ void __launch_bounds__(BS, 1024 / BS) gdi_cta_sorted_kernel(GdiDevPro
                 // which the partner must have read as this class's c0 first)
                 pair_sync();
                 int32_t k_seq = 0;                       // first window the ordered tail replays
+                if (split) {
+                    // the partner's stage maps copied in at once (one remote round trip), into the
+                    // slots of its windows, which this block does not use itself
+                    const int32_t pkb = crank ? 0 : kmid, pke = crank ? kmid : nwin;
+                    const uint4 *src = reinterpret_cast<const uint4 *>(peer(C.wmaps) + 2 * pkb);
+                    uint4 *dst = reinterpret_cast<uint4 *>(C.wmaps + 2 * pkb);
+                    for (int32_t i = threadIdx.x; i < 2 * (pke - pkb); i += BS) dst[i] = src[i];
+                    __syncthreads();
+                }
                 if (walk) {
                     // one thread follows x = G - c0 from 0 through the windows' stage maps (lattice
-                    // index t: x = 2 t - NT) up to the first window that leaves the lattice; in a
-                    // pair both blocks walk (the same result), the partner's maps read remotely
+                    // index t: x = 2 t - NT) up to the first window that leaves the lattice (in a
+                    // pair both blocks walk, to the same result)
                     if (threadIdx.x == 0) {
-                        const StageMap *own = C.wmaps, *other = PAIR ? peer(C.wmaps) : C.wmaps;
                         int t = NT / 2;
                         int32_t kf = nwin;
                         for (int32_t kk = 0; kk < nwin; ++kk) {
                             C.tin[kk] = t;
-                            const StageMap *wm = ((kk >= kmid) == (crank != 0)) ? own : other;
+                            const StageMap *wm = C.wmaps;
                             const int u = stage_apply(wm[2 * kk + (plus_first ? 1 : 0)],
                                                       stage_apply(wm[2 * kk + (plus_first ? 0 : 1)], t));
                             if (u < 0) { kf = kk; break; }
