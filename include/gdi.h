@@ -53,10 +53,14 @@ extern "C" {
 
 /* kernel paths (gdi_configure) */
 #define GDI_PATH_AUTO 0   /* several instances: CTA-resident.  One instance (W >= 1): the path a
-                             cost model fitted on GB300 predicts faster: the grid-scale path for a
-                             few replicas of a graph above about 3,000 vertices, or whenever the
-                             CTA path's shared memory does not fit; CTA-resident otherwise      */
-#define GDI_PATH_CTA  1   /* one thread block anneals one (instance, replica), spins in shared memory */
+                             cost model fitted on GB300 predicts faster (per colour class and per
+                             vertex + edge): the grid-scale path for a few replicas of a graph
+                             above a few thousand vertices, or whenever the CTA path's shared
+                             memory does not fit; CTA-resident otherwise                         */
+#define GDI_PATH_CTA  1   /* one thread block anneals one (instance, replica), spins in shared
+                             memory; with 1 <= W <= 256, when the items fill at most half of the
+                             SMs and the largest class has 8 to 128 windows, a cluster of two
+                             blocks anneals each item (gdi_last_launch counts both blocks)       */
 #define GDI_PATH_GRID 2   /* one instance over every SM (needs W >= 1); up to 8 replicas per pass;
                              W <= 256: sorted-window kernel, W > 256: tabulated-window kernel */
 
