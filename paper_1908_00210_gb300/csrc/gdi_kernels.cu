@@ -591,12 +591,21 @@ __global__ void __launch_bounds__(BS, 1024 / BS) gdi_cta_sorted_kernel(GdiDevPro
                 const int32_t kb = crank ? kmid : 0, ke = crank ? nwin : kmid;
                 const int32_t rb = min(kb * W, ns), re = min(ke * W, ns);     // my ranks in the class
                 const int32_t nown = re - rb;
-                // lanes per rank for the field sums: a small class of long rows spreads each row
-                // over a team of T lanes (one round of the block); otherwise one thread takes an
-                // aligned quad of ranks with one Philox call
-                int T = 1;
-                while (T < 32 && T < mean_deg && 2 * T * nown <= BS) T <<= 1;
-                if (T == 1) {
+                // the field sums' longest chain of dependent reads decides the layout: one thread
+                // per aligned quad of ranks (one Philox call per quad; per round 4 rows), or a team
+                // of T lanes per rank (T a power of two; per round a row / T); a round also costs
+                // about 4 reads of draw and reduction latency, and the team layout, which draws
+                // per rank, must shorten the chain by a quarter
+                int T = 0;
+                {
+                    const int32_t nq = (nown + 3) / 4 + 1;
+                    int32_t best = ((nq + BS - 1) / BS) * (4 * mean_deg + 4) * 3 / 4;
+                    for (int t = 1; t <= 32; t <<= 1) {
+                        const int32_t chain = ((nown * t + BS - 1) / BS) * ((mean_deg + t - 1) / t + 4);
+                        if (chain < best) { best = chain; T = t; }
+                    }
+                }
+                if (T == 0) {
                     for (int32_t qd = ((lo + rb) >> 2) + threadIdx.x; nown > 0 && qd <= ((lo + re - 1) >> 2); qd += BS) {
                         const uint4 u4 = philox4x32_10(
                             make_uint4((uint32_t)qd, (uint32_t)sw, (uint32_t)q, (uint32_t)rep), R.key0, R.key1);
