@@ -47,15 +47,15 @@ WORKLOADS = {
     # spins + 2 B.
     "torus100_r64": dict(kind="torus", L=100, gseed=2002, A=1, B=4, W=256, replicas=64,
                          sweeps=5000, t0=12.0, t1=0.2, seed=1,
-                         roofline=dict(bound="hbm", bytes_per_update=26, traffic=2_930_000,
-                                       traffic_l2=54_740_000_000,
+                         roofline=dict(bound="hbm", bytes_per_update=26, traffic=2_480_000,
+                                       traffic_l2=54_630_000_000,
                                        note="a pair of blocks per replica on 128 of 152 SMs; the graph "
                                             "is L1/L2-resident (90 % L1 hits); issue- and barrier-bound")),
     # Erdos-Renyi n = 800, p = 0.06, unit weights, greedy colouring, 1000 sweeps, 1 replica: one
     # block holds the whole instance; latency-bound.  Bytes per update 4 d + 4 + d + 2 at d = 48.7.
     "er800": dict(kind="er", n=800, p=0.06, gseed=1001, A=1, B=4, W=64, replicas=1, sweeps=1000,
                   t0=12.0, t1=0.2, seed=1,
-                  roofline=dict(bound="hbm", bytes_per_update=249.5, traffic=589_570, traffic_l2=8_130_000,
+                  roofline=dict(bound="hbm", bytes_per_update=249.5, traffic=655_620, traffic_l2=11_920_000,
                                 note="one block on one SM: latency-bound (19 colour classes of about "
                                      "42 vertices per sweep)")),
     # 4,096 Erdos-Renyi instances, n ~ U[800, 3000], mean degree ~ U[3, 48], unit or +-1 weights,
@@ -63,8 +63,8 @@ WORKLOADS = {
     # update at the batch's mean degree d = 25.5: 4 d + 4 + d + 2 = 134 B.
     "batched4096": dict(kind="batch", count=4096, gseed=3000, n_lo=800, n_hi=3000, A=1, B=4, W=256,
                         replicas=1, sweeps=2000, t0=12.0, t1=0.2, seed=11,
-                        roofline=dict(bound="hbm", bytes_per_update=134, traffic=666_293_000_000,
-                                      traffic_l2=2_020_000_000_000,
+                        roofline=dict(bound="hbm", bytes_per_update=134, traffic=685_297_000_000,
+                                      traffic_l2=1_850_000_000_000,
                                       note="the 4,096 graphs do not fit in L2: DRAM traffic is about a "
                                            "third of the algorithmic bytes, at 5 % of the measured HBM "
                                            "bandwidth; latency-bound")),
