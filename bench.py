@@ -66,7 +66,7 @@ WORKLOADS = {
                         roofline=dict(bound="hbm", bytes_per_update=134, traffic=685_297_000_000,
                                       traffic_l2=1_850_000_000_000,
                                       note="the 4,096 graphs do not fit in L2: DRAM traffic is about a "
-                                           "third of the algorithmic bytes, at 5 % of the measured HBM "
+                                           "third of the algorithmic bytes, at 6 % of the measured HBM "
                                            "bandwidth; latency-bound")),
 }
 DEFAULT_WORKLOAD = "ba1m_r8"
