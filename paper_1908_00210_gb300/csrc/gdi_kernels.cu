@@ -412,12 +412,14 @@ __global__ void __launch_bounds__(BS) gdi_cta_anneal_kernel(GdiDevProblem P, Gdi
 
 // ---------------------------------------------------------------------------------------------
 // CTA-resident sorted-window kernel (1 <= W <= 256): the same results as gdi_cta_anneal_kernel with
-// far fewer block barriers per window.  Per colour class: every thread computes the thresholds of
-// its ranks of the class (fields gathered from the shared spins); every warp sorts whole windows
-// of the class (window_maps: one comparison value per member, valid for any G entering the window,
-// gdi_window.cuh); then one warp replays the windows in rank order from the class-start G -- each
-// window two rounds of ballots -- and the flips are applied.  The windows of a class share no edge,
-// so only the running G passes from one window to the next.  SL = members per lane of a window.
+// far fewer block barriers per window.  Per colour class: the thresholds of the class's ranks
+// (fields gathered from the shared spins); every warp sorts whole windows of the class
+// (window_maps: one comparison value per member, valid for any G entering the window, and the
+// window's stage maps on the lattice, gdi_window.cuh); one thread walks the stage maps from the
+// class-start G, every window entered on the lattice is replayed at once by its own warp -- two
+// rounds of ballots -- and the rest in rank order; then the flips are applied.  The windows of a
+// class share no edge, so only the running G passes from one window to the next.  SL = members per
+// lane of a window.
 struct SortedCta {
     int32_t *gam;       // [max_class] flip thresholds of the class
     int16_t *rel;       // [max_class] comparison values
@@ -485,9 +487,9 @@ __host__ __device__ inline size_t cta_sorted_smem(int32_t max_n, int32_t max_cla
 
 // PAIR: a cluster of two blocks anneals each item.  Both keep all spins and G; a class of 3 to
 // nwm windows is split in two halves of windows (thresholds, sorts and replays each block's own),
-// the walk reads the other block's stage maps through distributed shared memory, and each block
-// applies the whole class's flips from both blocks' bitmaps.  Other classes are done by block 0
-// alone.  Flip bitmaps alternate between two buffers from class to class, so a block may clear
+// each block copies the other's stage maps in through distributed shared memory and walks all of
+// them, and each block applies the whole class's flips from both blocks' bitmaps.  Other classes
+// are done by block 0 alone.  Flip bitmaps alternate between two buffers from class to class, so a block may clear
 // the next class's buffer while its partner still reads the current one.
 template <int BS, int SL, bool PAIR>
 __global__ void __launch_bounds__(BS, 1024 / BS) gdi_cta_sorted_kernel(GdiDevProblem P, GdiDevRun R)
