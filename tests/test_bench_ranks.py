@@ -60,3 +60,17 @@ def test_job_throughput_is_weak_scaling():
     import bench
     assert bench.job_throughput(1, 4e9, 100.0) == pytest.approx(4e10)
     assert bench.job_throughput(8, 4e9, 100.0) == pytest.approx(3.2e11)
+
+
+def test_oracle_baseline_sample_fills_its_budget():
+    """The CPU baseline times the oracle on a bounded sample: a schedule shorter than the budget is
+    annealed again with other seeds until the budget is spent, and the sample text states what ran."""
+    import bench
+    from gdi_synth import erdos_renyi
+    g = erdos_renyi(120, 0.05, 3)
+    wl = dict(A=1, B=4, W=16, t0=12.0, t1=0.2, sweeps=20, seed=1, replicas=1)
+    v, cores, sample = bench.oracle_throughput(g, wl, seconds=1.0, processes=2)
+    assert v > 0 and cores == 2
+    assert "first 20 of 20 sweeps" in sample
+    anneals = float(sample.split(" x ")[1].split()[0])
+    assert anneals > 1.0            # the whole schedule takes far less than the budget
