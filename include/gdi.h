@@ -129,7 +129,9 @@ typedef struct {
  * 0xBF58476D1CE4E5B9; z = (z ^ z>>27) * 0x94D049BB133111EB; z ^= z>>31), a fixed pseudo-random
  * order inside the class; gdi_rank_space returns it.  This is the update order of the deterministic
  * reading of Algorithm 3 (Section 5.3): classes in order, each class in windows of W consecutive
- * ranks.  Host-side preprocessing; blocking. */
+ * ranks.  Device memory: the rank-space CSR (8 B per vertex + 4 B per directed edge), plus a
+ * 16-bit copy of the columns (2 B per directed edge) when every instance has at most 32,767
+ * vertices, and the spins (1 B per vertex per replica).  Host-side preprocessing; blocking. */
 int gdi_create(gdi_ctx **out, const gdi_graph *graph, const gdi_model *model);
 
 /* Anneal every replica of every instance with Algorithm 3, serialised deterministically: colour
