@@ -1,4 +1,5 @@
-"""Build libgdi.so in-tree for sm_103a with nvcc (one -gencode, both translation units in one call)."""
+"""Build libgdi.so in-tree for sm_103a with nvcc (one -gencode, every translation unit in one call,
+compiled in parallel on all host cores)."""
 from __future__ import annotations
 
 import os
@@ -10,7 +11,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 LIB = os.path.join(PKG, "libgdi.so")
 SOURCES = ["gdi_kernels.cu", "gdi_grid.cu", "gdi_static.cu", "gdi_mpnn.cu", "gdi_api.cpp"]
-HEADERS = ["gdi_internal.h", "gdi_device.cuh", os.path.join(ROOT, "include", "gdi.h"), os.path.join(ROOT, "include", "gdi_mpnn.h")]
+HEADERS = ["gdi_internal.h", "gdi_device.cuh", "gdi_window.cuh", os.path.join(ROOT, "include", "gdi.h"),
+           os.path.join(ROOT, "include", "gdi_mpnn.h")]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 
@@ -33,7 +35,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         return LIB
     tmp = LIB + f".tmp{os.getpid()}"
     cmd = [_nvcc(), ARCH, "-O3", "-lineinfo", "-std=c++17", "-shared", "-Xcompiler", "-fPIC",
-           "-Xcompiler", "-O2", "--threads", "4", "-I", os.path.join(ROOT, "include"), "-I", CSRC,
+           "-Xcompiler", "-O2", "--threads", "0", "-I", os.path.join(ROOT, "include"), "-I", CSRC,
            "-o", tmp] + [os.path.join(CSRC, s) for s in SOURCES] + ["-cudart", "shared"]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
